@@ -1,0 +1,159 @@
+/*
+ * tgp.h -- C ABI of the GB300 (sm_103a) library for population-wide fitness
+ * evaluation of tensorized tree-based genetic programming.
+ *
+ * Method: arXiv 2501.17168 ("EvoGP").  The population is the paper's three
+ * NaN-padded tensors (Sec. III-A): node types, node values and subtree sizes,
+ * each [pop, max_len] row-major.  Each tree is interpreted over every data
+ * point (Sec. II-A node semantics; Sec. III-C evaluation of the prefix
+ * encoding) and reduced to a mean squared error against the targets
+ * (Sec. III-C, symbolic-regression fitness).  Multi-output trees use Modi
+ * nodes (Sec. IV-C).  Reverse-mode gradients and the batched persistent
+ * launch are additions of this library; the paper has no counterpart.
+ *
+ * Encoding of one node (the paper leaves the codes open; this is the
+ * library's fixed reading):
+ *   type  0 variable, 1 constant, 2 unary function, 3 binary function;
+ *         18 / 19 are unary / binary Modi function nodes (16 + 2, 16 + 3).
+ *   value variable: feature index (integer in [0, n_features));
+ *         constant: the constant (finite);
+ *         function: func_id + 256 * out_index, an integer below 65536, where
+ *         out_index (Modi nodes only, 0 on plain nodes) is in [0, n_outputs).
+ *   size  the subtree size; size[0] is the tree length len (1..max_len).
+ *   Entries at positions >= len are never read.
+ * Functions (first prefix child = left operand):
+ *   0 add, 1 sub, 2 mul, 3 pdiv(a,b) = |b| > 1e-6f ? a/b : 1,
+ *   4 max (IEEE fmax), 5 sin, 6 cos, 7 plog(a) = |a| > 1e-6f ? log|a| : 0,
+ *   8 cexp(a) = exp(min(a, 80)), 9 tan.
+ * Outputs: with n_outputs == 1 and no Modi node in the tree the output is the
+ * root value; otherwise output k is the sum of the function values of the
+ * Modi nodes tagged k (0 if none), and a Modi node hands its parent the value
+ * of its rightmost child.
+ *
+ * Conventions for every entry point:
+ *   - Pointers marked [device] are CUDA device memory owned by the caller;
+ *     [host] pointers are host memory owned by the caller.
+ *   - The library never allocates, frees or synchronizes.  All work is
+ *     enqueued on `stream` (a cudaStream_t; NULL = legacy default stream) and
+ *     is asynchronous; the calls are legal inside CUDA stream capture.
+ *   - Scratch memory is the caller's workspace `ws` of `ws_bytes` bytes
+ *     ([device], 256-byte aligned), sized by tgp_workspace_size for the same
+ *     arguments.  It may be reused by the next call on the same stream.
+ *   - Argument errors (null pointer, bad size, short workspace, unsupported
+ *     shape) are returned synchronously and nothing is launched.
+ *   - Per-tree problems found on the device are reported in tree_status
+ *     (bitmask below); that tree's outputs, MSE and gradients are NaN and the
+ *     call still returns TGP_OK.
+ *   - Computation is FP32; the per-tree MSE is accumulated in FP64.
+ */
+#ifndef TGP_H
+#define TGP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TGP_OK = 0,
+  TGP_ERR_INVALID_ARG = 1,  /* null pointer, negative or inconsistent size   */
+  TGP_ERR_INVALID_TREE = 2, /* reserved: trees are reported per tree          */
+  TGP_ERR_WORKSPACE = 3,    /* ws null, misaligned or smaller than required  */
+  TGP_ERR_CUDA = 4,         /* a CUDA runtime call failed (launch, attribute) */
+  TGP_ERR_TIMEOUT = 5,      /* reported by tgp_check_device_error            */
+  TGP_ERR_UNSUPPORTED = 6   /* shape beyond the library limits               */
+} tgp_status;
+
+/* Per-tree status bits (Sec. III-A encoding rules). */
+enum {
+  TGP_TREE_OK = 0,
+  TGP_TREE_LEN = 1,     /* size[0] not an integer in [1, max_len]                 */
+  TGP_TREE_TYPE = 2,    /* a type code not in {0,1,2,3,18,19}                    */
+  TGP_TREE_FUNC = 4,    /* function id unknown, arity disagrees with the type,
+                           or an output index on a plain function node           */
+  TGP_TREE_VAR = 8,     /* variable index not an integer in [0, n_features)      */
+  TGP_TREE_MODI = 16,   /* Modi output index not in [0, n_outputs)               */
+  TGP_TREE_CONST = 32,  /* constant not finite                                   */
+  TGP_TREE_SIZE = 64,   /* subtree sizes disagree with the prefix structure      */
+  TGP_TREE_DEPTH = 128  /* needs more evaluation registers than the kernel has   */
+};
+
+/* Library limits. */
+#define TGP_MAX_LEN 1024       /* largest supported max_len                */
+#define TGP_MAX_OUTPUTS 16     /* largest supported n_outputs              */
+#define TGP_MAX_FEATURES 256   /* largest supported n_features             */
+
+/* The paper's population tensors P_type, P_val, P_size (Sec. III-A). */
+typedef struct tgp_population {
+  const float* type;  /* [device] [pop, ld]                                  */
+  const float* value; /* [device] [pop, ld]                                  */
+  const float* size;  /* [device] [pop, ld]                                  */
+  int64_t pop;        /* number of trees P >= 0                              */
+  int32_t max_len;    /* |T|_max, 1..TGP_MAX_LEN                             */
+  int64_t ld;         /* row stride in elements, ld >= max_len               */
+} tgp_population;
+
+/* Feature matrix X [n_points, n_features] row-major with row stride ldx. */
+typedef struct tgp_data {
+  const float* X;     /* [device]                                            */
+  int64_t n_points;   /* D >= 0                                              */
+  int32_t n_features; /* F, 1..TGP_MAX_FEATURES                              */
+  int64_t ldx;        /* row stride in elements, ldx >= n_features           */
+} tgp_data;
+
+/* Launch shape of the evaluation kernels.  Zero fields take the library's
+ * heuristic; the autotuner fills them from measurements. */
+typedef struct tgp_config {
+  int32_t trees_per_block;  /* trees staged together in shared memory (1..64) */
+  int32_t points_per_tile;  /* points of X staged per tile; a multiple of
+                               32 * points_per_lane (up to 4096)              */
+  int32_t tiles_per_item;   /* consecutive tiles one work item sweeps         */
+  int32_t points_per_lane;  /* 4 or 8 points evaluated per thread             */
+} tgp_config;
+
+/* Bytes of workspace the calls below need for these arguments (0 on invalid
+ * arguments).  cfg may be NULL. */
+size_t tgp_workspace_size(const tgp_population* pop, const tgp_data* data, int32_t n_outputs,
+                          const tgp_config* cfg);
+
+/* Validates every tree (Sec. III-A rules) and writes tree_status [device]
+ * [pop] int32.  Also compiles the trees into the workspace. */
+tgp_status tgp_validate(const tgp_population* pop, int32_t n_features, int32_t n_outputs,
+                        int32_t* tree_status, void* ws, size_t ws_bytes, void* stream);
+
+/* Forward outputs (Sec. II-A, Sec. IV-C): out [device] float [pop, n_outputs,
+ * n_points]; tree_status [device] int32 [pop] or NULL. */
+tgp_status tgp_eval_forward(const tgp_population* pop, const tgp_data* data, int32_t n_outputs,
+                            float* out, int32_t* tree_status, void* ws, size_t ws_bytes,
+                            void* stream);
+tgp_status tgp_eval_forward_cfg(const tgp_population* pop, const tgp_data* data,
+                                int32_t n_outputs, float* out, int32_t* tree_status, void* ws,
+                                size_t ws_bytes, void* stream, const tgp_config* cfg);
+
+/* SR fitness (Sec. III-C): mse [device] double [pop, n_outputs] with
+ * mse[p,k] = (1/D) sum_d (o_k(x_d) - y[d,k])^2; y [device] float
+ * [n_points, n_outputs] row-major (contiguous).  n_points must be >= 1. */
+tgp_status tgp_fitness_mse(const tgp_population* pop, const tgp_data* data, const float* y,
+                           int32_t n_outputs, double* mse, int32_t* tree_status, void* ws,
+                           size_t ws_bytes, void* stream);
+tgp_status tgp_fitness_mse_cfg(const tgp_population* pop, const tgp_data* data, const float* y,
+                               int32_t n_outputs, double* mse, int32_t* tree_status, void* ws,
+                               size_t ws_bytes, void* stream, const tgp_config* cfg);
+
+/* Reads and clears the device error word left in ws by the last calls on
+ * this workspace (a bounded wait that gave up).  Synchronizes `stream`.
+ * Returns TGP_OK or TGP_ERR_TIMEOUT. */
+tgp_status tgp_check_device_error(void* ws, size_t ws_bytes, void* stream);
+
+/* Human-readable name of a status code. */
+const char* tgp_status_string(tgp_status s);
+
+/* Library version string. */
+const char* tgp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TGP_H */

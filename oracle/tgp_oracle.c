@@ -32,7 +32,7 @@
  *           +16 marks a function node as a Modi node (18, 19).
  *   value : variable -> feature index; constant -> the constant;
  *           function -> func_id + 256 * output_index (output_index only on
- *           Modi nodes, 0 otherwise).
+ *           Modi nodes, 0 otherwise); an integer below 65536.
  *   func  : 0 add, 1 sub, 2 mul, 3 protected div, 4 max (binary);
  *           5 sin, 6 cos, 7 protected log, 8 clamped exp, 9 tan (unary).
  *   The first prefix child is the left operand: [sub, a, b] = a - b.
@@ -117,7 +117,7 @@ int orc_validate_one(const float* type, const float* val, const float* size,
   int st = 0;
   for (int i = 0; i < len; ++i) {
     double tv = type[i], vv = val[i];
-    int ty = is_int(tv) ? (int)tv : -1;
+    int ty = (is_int(tv) && tv >= 0 && tv < 64) ? (int)tv : -1;
     int base = ty >= 0 ? (ty & ~T_MODI) : -1;
     int modi = ty >= 0 && (ty & T_MODI);
     if (!(ty == 0 || ty == 1 || ty == 2 || ty == 3 || ty == 18 || ty == 19)) { st |= ST_TYPE; continue; }
@@ -126,7 +126,7 @@ int orc_validate_one(const float* type, const float* val, const float* size,
     } else if (base == T_CONST) {
       if (!isfinite(vv)) st |= ST_CONST;
     } else {
-      if (!is_int(vv) || vv < 0) { st |= ST_FUNC; continue; }
+      if (!is_int(vv) || vv < 0 || vv >= 65536) { st |= ST_FUNC; continue; }
       long iv = (long)vv;
       int f = (int)(iv % 256);
       long o = iv / 256;
@@ -195,7 +195,11 @@ static double trig_abs(void) { return 6.9053396600248786e-07; /* 2^-20.5 */ }
  * an absolute error of at most FLT_MIN. */
 static double err_of_raw(int f, double a, double ea, double b, double eb, double v);
 static double err_of(int f, double a, double ea, double b, double eb, double v) {
-  return err_of_raw(f, a, ea, b, eb, v) + FLT_MIN;
+  /* an operand whose own bound is infinite (or undefined) may be anything:
+   * so may the result (this also keeps 0 * inf from turning into NaN) */
+  if (!(ea < INFINITY) || !(eb < INFINITY)) return INFINITY;
+  double e = err_of_raw(f, a, ea, b, eb, v);
+  return e != e ? INFINITY : e + FLT_MIN;
 }
 static double err_of_raw(int f, double a, double ea, double b, double eb, double v) {
   double av = fabs(v);

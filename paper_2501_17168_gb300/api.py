@@ -1,0 +1,163 @@
+"""PyTorch-facing binding of the C ABI.
+
+Same entry-point names as ``include/tgp.h``.  These functions only marshal
+arguments: they check dtypes and shapes, allocate the outputs and the
+workspace as torch device tensors (torch is the memory manager), and pass raw
+device pointers plus the current CUDA stream to ``libtgp.so``.  Every step of
+the evaluation runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import check, tgp_config, tgp_data, tgp_population
+
+_WS: dict = {}
+
+
+def _stream_handle(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def workspace(nbytes: int, device) -> torch.Tensor:
+    """A cached uint8 workspace of at least nbytes on device (per stream)."""
+    key = (torch.device(device).index, _stream_handle(device))
+    ws = _WS.get(key)
+    if ws is None or ws.numel() < nbytes:
+        ws = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+        _WS[key] = ws
+    return ws
+
+
+def _f32(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32")
+    return t
+
+
+def make_population(type_, val, size, max_len: int | None = None) -> tgp_population:
+    for name, t in (("type", type_), ("value", val), ("size", size)):
+        _f32(t, name)
+        if t.dim() != 2 or t.stride(1) != 1:
+            raise ValueError(f"{name} must be [pop, ld] with unit column stride")
+    if not (type_.shape == val.shape == size.shape and type_.stride() == val.stride() == size.stride()):
+        raise ValueError("type, value and size must share shape and strides")
+    P, L = type_.shape
+    ld = type_.stride(0) if P > 1 else L
+    return tgp_population(type_.data_ptr(), val.data_ptr(), size.data_ptr(), P,
+                          int(max_len if max_len is not None else L), max(ld, L))
+
+
+def make_data(X) -> tgp_data:
+    _f32(X, "X")
+    if X.dim() != 2:
+        raise ValueError("X must be [n_points, n_features]")
+    D, F = X.shape
+    if D > 0 and F > 1 and X.stride(1) != 1:
+        raise ValueError("X must have unit column stride")
+    ldx = X.stride(0) if D > 1 else F
+    return tgp_data(X.data_ptr(), D, F, max(ldx, F))
+
+
+def make_config(cfg) -> tgp_config | None:
+    if cfg is None:
+        return None
+    if isinstance(cfg, tgp_config):
+        return cfg
+    return tgp_config(int(cfg.get("trees_per_block", 0)), int(cfg.get("points_per_tile", 0)),
+                      int(cfg.get("tiles_per_item", 0)), int(cfg.get("points_per_lane", 0)))
+
+
+def _cref(c):
+    return ctypes.byref(c) if c is not None else None
+
+
+def tgp_workspace_size(type_, val, size, X=None, n_outputs: int = 1, max_len=None, config=None) -> int:
+    lib = _lib.load()
+    pop = make_population(type_, val, size, max_len)
+    data = make_data(X) if X is not None else None
+    n = lib.tgp_workspace_size(ctypes.byref(pop), _cref(data), n_outputs, _cref(make_config(config)))
+    if n == 0:
+        raise _lib.TGPError(_lib.TGP_ERR_INVALID_ARG, "tgp_workspace_size")
+    return int(n)
+
+
+def tgp_validate(type_, val, size, n_features: int, n_outputs: int = 1, max_len=None) -> torch.Tensor:
+    """Per-tree status bitmask (int32 [pop])."""
+    lib = _lib.load()
+    pop = make_population(type_, val, size, max_len)
+    dev = type_.device
+    st = torch.empty(pop.pop, dtype=torch.int32, device=dev)
+    n = lib.tgp_workspace_size(ctypes.byref(pop), None, n_outputs, None)
+    ws = workspace(n, dev)
+    check(lib.tgp_validate(ctypes.byref(pop), n_features, n_outputs, st.data_ptr(), ws.data_ptr(),
+                           ws.numel(), _stream_handle(dev)), "tgp_validate")
+    return st
+
+
+def tgp_eval_forward(type_, val, size, X, n_outputs: int = 1, max_len=None, config=None,
+                     out=None, tree_status=None):
+    """Forward outputs [pop, n_outputs, n_points] float32 and tree status."""
+    lib = _lib.load()
+    pop = make_population(type_, val, size, max_len)
+    data = make_data(X)
+    dev = X.device
+    if out is None:
+        out = torch.empty((pop.pop, n_outputs, data.n_points), dtype=torch.float32, device=dev)
+    if tree_status is None:
+        tree_status = torch.empty(pop.pop, dtype=torch.int32, device=dev)
+    cfg = make_config(config)
+    n = lib.tgp_workspace_size(ctypes.byref(pop), ctypes.byref(data), n_outputs, _cref(cfg))
+    if n == 0:
+        raise _lib.TGPError(_lib.TGP_ERR_INVALID_ARG, "tgp_workspace_size")
+    ws = workspace(n, dev)
+    check(lib.tgp_eval_forward_cfg(ctypes.byref(pop), ctypes.byref(data), n_outputs, out.data_ptr(),
+                                   tree_status.data_ptr(), ws.data_ptr(), ws.numel(),
+                                   _stream_handle(dev), _cref(cfg)), "tgp_eval_forward")
+    return out, tree_status
+
+
+def tgp_fitness_mse(type_, val, size, X, y, n_outputs: int = 1, max_len=None, config=None,
+                    mse=None, tree_status=None):
+    """Per-tree, per-output MSE [pop, n_outputs] float64 and tree status."""
+    lib = _lib.load()
+    pop = make_population(type_, val, size, max_len)
+    data = make_data(X)
+    _f32(y, "y")
+    if not y.is_contiguous() or y.numel() != data.n_points * n_outputs:
+        raise ValueError("y must be a contiguous [n_points, n_outputs] float32 tensor")
+    dev = X.device
+    if mse is None:
+        mse = torch.empty((pop.pop, n_outputs), dtype=torch.float64, device=dev)
+    if tree_status is None:
+        tree_status = torch.empty(pop.pop, dtype=torch.int32, device=dev)
+    cfg = make_config(config)
+    n = lib.tgp_workspace_size(ctypes.byref(pop), ctypes.byref(data), n_outputs, _cref(cfg))
+    if n == 0:
+        raise _lib.TGPError(_lib.TGP_ERR_INVALID_ARG, "tgp_workspace_size")
+    ws = workspace(n, dev)
+    check(lib.tgp_fitness_mse_cfg(ctypes.byref(pop), ctypes.byref(data), y.data_ptr(), n_outputs,
+                                  mse.data_ptr(), tree_status.data_ptr(), ws.data_ptr(), ws.numel(),
+                                  _stream_handle(dev), _cref(cfg)), "tgp_fitness_mse")
+    return mse, tree_status
+
+
+def tgp_check_device_error(device=None):
+    """Raises if a bounded device-side wait gave up during the last call."""
+    lib = _lib.load()
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    ws = _WS.get((dev.index, _stream_handle(dev)))
+    if ws is None:
+        return
+    check(lib.tgp_check_device_error(ws.data_ptr(), ws.numel(), _stream_handle(dev)),
+          "tgp_check_device_error")
+
+
+def population_to(pop, device) -> tuple:
+    """workloads.Population -> (type, value, size) float32 device tensors."""
+    return tuple(torch.from_numpy(a).to(device) for a in (pop.type, pop.val, pop.size))

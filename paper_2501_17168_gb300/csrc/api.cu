@@ -1,0 +1,385 @@
+// api.cu -- host side of the C ABI declared in include/tgp.h: argument
+// checks, launch-shape heuristic, workspace layout and kernel launches.  No
+// allocation, no synchronization; everything goes onto the caller's stream.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/tgp.h"
+#include "tgp_internal.cuh"
+
+namespace tgp {
+size_t stage_smem_bytes();
+int stage_threads();
+const void* stage_kernel_ptr();
+const void* find_eval_kernel(int K, int nw, bool modi, bool out);
+size_t eval_smem_bytes(int K, int nw, bool modi, bool mse, int bt, int pcap, int tp, int F, int O);
+const void* finalize_kernel_ptr();
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+constexpr int kNW = 8;
+
+struct DevInfo {
+  bool init = false;
+  int sms = 0;
+  int smem_optin = 0;
+};
+std::mutex g_mu;
+DevInfo g_dev[kMaxDevices];
+
+struct AttrEntry {
+  const void* fn;
+  int dev;
+  int bytes;
+};
+AttrEntry g_attr[256];
+int g_nattr = 0;
+
+bool dev_info(DevInfo* out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return false;
+  std::lock_guard<std::mutex> lk(g_mu);
+  DevInfo& d = g_dev[dev];
+  if (!d.init) {
+    if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+        cudaSuccess)
+      return false;
+    d.init = true;
+  }
+  *out = d;
+  return true;
+}
+
+// Raises the dynamic shared memory limit of fn on the current device once.
+bool ensure_smem(const void* fn, size_t bytes) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (int i = 0; i < g_nattr; ++i)
+    if (g_attr[i].fn == fn && g_attr[i].dev == dev && g_attr[i].bytes >= (int)bytes) return true;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+    return false;
+  for (int i = 0; i < g_nattr; ++i)
+    if (g_attr[i].fn == fn && g_attr[i].dev == dev) {
+      g_attr[i].bytes = (int)bytes;
+      return true;
+    }
+  if (g_nattr < 256) g_attr[g_nattr++] = {fn, dev, (int)bytes};
+  return true;
+}
+
+inline long long cdiv(long long a, long long b) { return (a + b - 1) / b; }
+inline size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+int pcap_of(int max_len) { return (max_len + 2 + 1) & ~1; }
+
+// Launch shape: the caller's config where given, else the heuristic.
+bool choose_shape(long long P, long long D, int F, int O, int max_len, const tgp_config* cfg,
+                  bool modi, bool mse, const DevInfo& dv, Shape* sh) {
+  Shape s{};
+  s.nw = kNW;
+  s.K = (cfg && cfg->points_per_lane) ? cfg->points_per_lane : (modi ? 4 : 8);
+  if (modi) s.K = 4;  // Modi accumulators live in shared memory: 4 points per lane
+  if (s.K != 4 && s.K != 8) return false;
+  const int CH = 32 * s.K;
+  const int pcap = pcap_of(max_len);
+  s.bt = (cfg && cfg->trees_per_block) ? cfg->trees_per_block : 16;
+  if (s.bt < 1 || s.bt > 64) return false;
+  const long long Dr = D < 1 ? 1 : D;
+  if (cfg && cfg->points_per_tile) {
+    s.tp = cfg->points_per_tile;
+    if (s.tp % CH != 0 || s.tp < CH || s.tp > 4096) return false;
+  } else {
+    s.tp = 4 * CH;
+    while (s.tp > CH && (long long)(s.tp / 2) >= Dr) s.tp /= 2;
+  }
+  const long long target = 4LL * dv.sms;  // enough items to balance a persistent grid
+  if (!(cfg && cfg->trees_per_block)) {
+    // small problems: fewer trees per block so that every SM gets work
+    while (s.bt > 1 && cdiv(P, s.bt) * cdiv(Dr, s.tp) < target) s.bt /= 2;
+  }
+  // fit shared memory (two CTAs per SM when possible)
+  const size_t limit = (size_t)dv.smem_optin;
+  auto bytes = [&]() { return eval_smem_bytes(s.K, s.nw, modi, mse, s.bt, pcap, s.tp, F, O); };
+  while (bytes() > limit && s.tp > CH && !(cfg && cfg->points_per_tile)) s.tp /= 2;
+  while (bytes() > limit && s.bt > 1 && !(cfg && cfg->trees_per_block)) s.bt /= 2;
+  if (bytes() > limit) return false;
+  s.n_tiles = (int)cdiv(Dr, s.tp);
+  s.n_blocks = (int)cdiv(P < 1 ? 1 : P, s.bt);
+  if (cfg && cfg->tiles_per_item) {
+    s.g = cfg->tiles_per_item;
+    if (s.g < 1) return false;
+  } else {
+    s.g = (int)cdiv(s.n_tiles, 64);  // at most 64 partial sums per tree and output
+    while (s.g > 1 && (long long)s.n_blocks * cdiv(s.n_tiles, s.g) < target) s.g /= 2;
+    if (s.g < 1) s.g = 1;
+    if (cdiv(s.n_tiles, s.g) > 64) s.g = (int)cdiv(s.n_tiles, 64);
+  }
+  s.n_groups = (int)cdiv(s.n_tiles, s.g);
+  s.n_items = (long long)s.n_blocks * s.n_groups;
+  *sh = s;
+  return true;
+}
+
+WsLayout ws_layout(long long P, int max_len, int O, int n_groups) {
+  WsLayout w{};
+  w.pcap = pcap_of(max_len);
+  w.n_groups = n_groups;
+  size_t off = 0;
+  w.ctrl = off; off = al256(off + CTRL_WORDS * 4);
+  w.prog = off; off = al256(off + (size_t)P * w.pcap * 8);
+  w.plen = off; off = al256(off + (size_t)P * 4);
+  w.status = off; off = al256(off + (size_t)P * 4);
+  w.partial = off; off = al256(off + (size_t)P * O * n_groups * 8);
+  w.total = off;
+  return w;
+}
+
+bool pop_ok(const tgp_population* p) {
+  if (!p || p->pop < 0 || p->max_len < 1 || p->max_len > TGP_MAX_LEN || p->ld < p->max_len) return false;
+  if (p->pop > 0 && (!p->type || !p->value || !p->size)) return false;
+  return true;
+}
+bool data_ok(const tgp_data* d) {
+  if (!d || d->n_points < 0 || d->n_features < 1 || d->n_features > TGP_MAX_FEATURES ||
+      d->ldx < d->n_features)
+    return false;
+  if (d->n_points > 0 && !d->X) return false;
+  return true;
+}
+
+tgp_status launch_stage(const tgp_population* pop, int F, int O, const WsLayout& w, char* ws,
+                        int32_t* user_status, cudaStream_t st, const DevInfo& dv) {
+  if (pop->pop == 0) return TGP_OK;
+  StageArgs a;
+  a.type = pop->type;
+  a.val = pop->value;
+  a.size = pop->size;
+  a.pop = pop->pop;
+  a.ld = pop->ld;
+  a.max_len = pop->max_len;
+  a.n_features = F;
+  a.n_outputs = O;
+  a.prog = reinterpret_cast<uint2*>(ws + w.prog);
+  a.pcap = w.pcap;
+  a.plen = reinterpret_cast<int*>(ws + w.plen);
+  a.status = reinterpret_cast<int*>(ws + w.status);
+  a.user_status = user_status;
+  a.ctrl = reinterpret_cast<unsigned*>(ws + w.ctrl);
+  const void* fn = stage_kernel_ptr();
+  size_t smem = stage_smem_bytes();
+  if (!ensure_smem(fn, smem)) return TGP_ERR_CUDA;
+  const int warps_per_cta = stage_threads() / 32;
+  long long grid = cdiv(pop->pop, warps_per_cta);
+  if (grid > (long long)dv.sms * 16) grid = (long long)dv.sms * 16;
+  void* args[] = {&a};
+  if (cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(stage_threads()), args, smem, st) != cudaSuccess)
+    return TGP_ERR_CUDA;
+  return TGP_OK;
+}
+
+// Launches the evaluation kernels (both variants for single-output
+// populations; each exits unless it matches the stage pass's Modi flag).
+tgp_status launch_eval(const tgp_population* pop, const tgp_data* data, const float* y, int O,
+                       float* out, const WsLayout& w, char* ws, const Shape& sh_plain,
+                       const Shape& sh_modi, cudaStream_t st, const DevInfo& dv, bool mse) {
+  for (int variant = 0; variant < 2; ++variant) {
+    const bool modi = variant == 1;
+    if (!modi && O > 1) continue;
+    const Shape& sh = modi ? sh_modi : sh_plain;
+    const void* fn = find_eval_kernel(sh.K, sh.nw, modi, !mse);
+    if (!fn) return TGP_ERR_UNSUPPORTED;
+    size_t smem = eval_smem_bytes(sh.K, sh.nw, modi, mse, sh.bt, w.pcap, sh.tp, data->n_features, O);
+    if (!ensure_smem(fn, smem)) return TGP_ERR_CUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, sh.nw * 32, smem) != cudaSuccess)
+      return TGP_ERR_CUDA;
+    if (per_sm < 1) return TGP_ERR_UNSUPPORTED;
+    long long grid = (long long)dv.sms * per_sm;
+    if (grid > sh.n_items) grid = sh.n_items;
+    EvalArgs a;
+    a.prog = reinterpret_cast<const uint2*>(ws + w.prog);
+    a.plen = reinterpret_cast<const int*>(ws + w.plen);
+    a.status = reinterpret_cast<const int*>(ws + w.status);
+    a.pcap = w.pcap;
+    a.pop = pop->pop;
+    a.X = data->X;
+    a.D = data->n_points;
+    a.F = data->n_features;
+    a.ldx = data->ldx;
+    a.y = y;
+    a.O = O;
+    a.out = out;
+    a.partial = reinterpret_cast<double*>(ws + w.partial);
+    a.bt = sh.bt;
+    a.tp = sh.tp;
+    a.g = sh.g;
+    a.n_tiles = sh.n_tiles;
+    a.n_groups = sh.n_groups;
+    a.n_blocks = sh.n_blocks;
+    a.n_items = sh.n_items;
+    a.ctrl = reinterpret_cast<unsigned*>(ws + w.ctrl);
+    void* args[] = {&a};
+    if (cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(sh.nw * 32), args, smem, st) != cudaSuccess)
+      return TGP_ERR_CUDA;
+  }
+  return TGP_OK;
+}
+
+// Shapes of both kernel variants share n_groups so one partial buffer serves.
+bool shapes_for(const tgp_population* pop, const tgp_data* data, int O, const tgp_config* cfg,
+                bool mse, const DevInfo& dv, Shape* plain, Shape* modi) {
+  long long D = data ? data->n_points : 0;
+  int F = data ? data->n_features : 1;
+  if (!choose_shape(pop->pop, D, F, O, pop->max_len, cfg, true, mse, dv, modi)) return false;
+  if (O == 1) {
+    if (!choose_shape(pop->pop, D, F, O, pop->max_len, cfg, false, mse, dv, plain)) return false;
+  } else {
+    *plain = *modi;
+  }
+  return true;
+}
+
+tgp_status run(const tgp_population* pop, const tgp_data* data, const float* y, int O, float* out,
+               double* mse_out, bool mse, int32_t* tree_status, void* ws, size_t ws_bytes,
+               void* stream, const tgp_config* cfg) {
+  if (!pop_ok(pop) || !data_ok(data) || O < 1 || O > TGP_MAX_OUTPUTS) return TGP_ERR_INVALID_ARG;
+  if (mse && (data->n_points < 1 || (pop->pop > 0 && (!y || !mse_out)))) return TGP_ERR_INVALID_ARG;
+  if (!mse && pop->pop > 0 && data->n_points > 0 && !out) return TGP_ERR_INVALID_ARG;
+  DevInfo dv;
+  if (!dev_info(&dv)) return TGP_ERR_CUDA;
+  Shape sp, sm;
+  if (!shapes_for(pop, data, O, cfg, mse, dv, &sp, &sm)) return TGP_ERR_UNSUPPORTED;
+  const int n_groups = sm.n_groups > sp.n_groups ? sm.n_groups : sp.n_groups;
+  WsLayout w = ws_layout(pop->pop, pop->max_len, O, mse ? n_groups : 0);
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < w.total) return TGP_ERR_WORKSPACE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* wsb = reinterpret_cast<char*>(ws);
+  if (cudaMemsetAsync(wsb + w.ctrl, 0, CTRL_WORDS * 4, st) != cudaSuccess) return TGP_ERR_CUDA;
+  tgp_status s = launch_stage(pop, data->n_features, O, w, wsb, tree_status, st, dv);
+  if (s != TGP_OK) return s;
+  if (pop->pop == 0 || data->n_points == 0) return TGP_OK;
+  // both variants must agree on n_groups for the shared partial layout
+  sp.n_groups = sm.n_groups = n_groups;
+  sp.g = (int)cdiv(sp.n_tiles, n_groups);
+  sm.g = (int)cdiv(sm.n_tiles, n_groups);
+  sp.n_items = (long long)sp.n_blocks * n_groups;
+  sm.n_items = (long long)sm.n_blocks * n_groups;
+  s = launch_eval(pop, data, y, O, out, w, wsb, sp, sm, st, dv, mse);
+  if (s != TGP_OK) return s;
+  if (mse) {
+    FinalArgs f;
+    f.partial = reinterpret_cast<const double*>(wsb + w.partial);
+    f.status = reinterpret_cast<const int*>(wsb + w.status);
+    f.mse = mse_out;
+    f.pop = pop->pop;
+    f.O = O;
+    f.n_groups = n_groups;
+    f.D = data->n_points;
+    void* args[] = {&f};
+    long long n = pop->pop * O;
+    if (cudaLaunchKernel(finalize_kernel_ptr(), dim3((unsigned)cdiv(n, 256)), dim3(256), args, 0, st) !=
+        cudaSuccess)
+      return TGP_ERR_CUDA;
+  }
+  return TGP_OK;
+}
+
+}  // namespace
+}  // namespace tgp
+
+using namespace tgp;
+
+extern "C" {
+
+size_t tgp_workspace_size(const tgp_population* pop, const tgp_data* data, int32_t n_outputs,
+                          const tgp_config* cfg) {
+  if (!pop_ok(pop) || n_outputs < 1 || n_outputs > TGP_MAX_OUTPUTS) return 0;
+  if (data && !data_ok(data)) return 0;
+  DevInfo dv;
+  if (!dev_info(&dv)) return 0;
+  int n_groups = 0;
+  if (data && data->n_points > 0) {
+    Shape sp, sm;
+    if (!shapes_for(pop, data, n_outputs, cfg, true, dv, &sp, &sm)) return 0;
+    n_groups = sm.n_groups > sp.n_groups ? sm.n_groups : sp.n_groups;
+  }
+  return ws_layout(pop->pop, pop->max_len, n_outputs, n_groups).total;
+}
+
+tgp_status tgp_validate(const tgp_population* pop, int32_t n_features, int32_t n_outputs,
+                        int32_t* tree_status, void* ws, size_t ws_bytes, void* stream) {
+  if (!pop_ok(pop) || n_features < 1 || n_features > TGP_MAX_FEATURES || n_outputs < 1 ||
+      n_outputs > TGP_MAX_OUTPUTS)
+    return TGP_ERR_INVALID_ARG;
+  if (pop->pop > 0 && !tree_status) return TGP_ERR_INVALID_ARG;
+  DevInfo dv;
+  if (!dev_info(&dv)) return TGP_ERR_CUDA;
+  WsLayout w = ws_layout(pop->pop, pop->max_len, n_outputs, 0);
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < w.total) return TGP_ERR_WORKSPACE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* wsb = reinterpret_cast<char*>(ws);
+  if (cudaMemsetAsync(wsb + w.ctrl, 0, CTRL_WORDS * 4, st) != cudaSuccess) return TGP_ERR_CUDA;
+  return launch_stage(pop, n_features, n_outputs, w, wsb, tree_status, st, dv);
+}
+
+tgp_status tgp_eval_forward_cfg(const tgp_population* pop, const tgp_data* data, int32_t n_outputs,
+                                float* out, int32_t* tree_status, void* ws, size_t ws_bytes,
+                                void* stream, const tgp_config* cfg) {
+  return run(pop, data, nullptr, n_outputs, out, nullptr, false, tree_status, ws, ws_bytes, stream,
+             cfg);
+}
+
+tgp_status tgp_eval_forward(const tgp_population* pop, const tgp_data* data, int32_t n_outputs,
+                            float* out, int32_t* tree_status, void* ws, size_t ws_bytes,
+                            void* stream) {
+  return run(pop, data, nullptr, n_outputs, out, nullptr, false, tree_status, ws, ws_bytes, stream,
+             nullptr);
+}
+
+tgp_status tgp_fitness_mse_cfg(const tgp_population* pop, const tgp_data* data, const float* y,
+                               int32_t n_outputs, double* mse, int32_t* tree_status, void* ws,
+                               size_t ws_bytes, void* stream, const tgp_config* cfg) {
+  return run(pop, data, y, n_outputs, nullptr, mse, true, tree_status, ws, ws_bytes, stream, cfg);
+}
+
+tgp_status tgp_fitness_mse(const tgp_population* pop, const tgp_data* data, const float* y,
+                           int32_t n_outputs, double* mse, int32_t* tree_status, void* ws,
+                           size_t ws_bytes, void* stream) {
+  return tgp_fitness_mse_cfg(pop, data, y, n_outputs, mse, tree_status, ws, ws_bytes, stream, nullptr);
+}
+
+tgp_status tgp_check_device_error(void* ws, size_t ws_bytes, void* stream) {
+  if (!ws || ws_bytes < CTRL_WORDS * 4) return TGP_ERR_WORKSPACE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  unsigned word = 0;
+  unsigned* ctrl = reinterpret_cast<unsigned*>(ws);
+  if (cudaMemcpyAsync(&word, ctrl + CTRL_ERROR, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return TGP_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return TGP_ERR_CUDA;
+  if (word != 0) {
+    if (cudaMemsetAsync(ctrl + CTRL_ERROR, 0, 4, st) != cudaSuccess) return TGP_ERR_CUDA;
+    return TGP_ERR_TIMEOUT;
+  }
+  return TGP_OK;
+}
+
+const char* tgp_status_string(tgp_status s) {
+  switch (s) {
+    case TGP_OK: return "TGP_OK";
+    case TGP_ERR_INVALID_ARG: return "TGP_ERR_INVALID_ARG";
+    case TGP_ERR_INVALID_TREE: return "TGP_ERR_INVALID_TREE";
+    case TGP_ERR_WORKSPACE: return "TGP_ERR_WORKSPACE";
+    case TGP_ERR_CUDA: return "TGP_ERR_CUDA";
+    case TGP_ERR_TIMEOUT: return "TGP_ERR_TIMEOUT";
+    case TGP_ERR_UNSUPPORTED: return "TGP_ERR_UNSUPPORTED";
+  }
+  return "TGP_ERR_UNKNOWN";
+}
+
+const char* tgp_version(void) { return "tgp-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,473 @@
+// eval.cu -- population forward evaluation and MSE fitness (Sec. III-C).
+//
+// Work decomposition.  A work item is (a block of bt trees) x (a group of g
+// consecutive point tiles of tp points).  A persistent grid of CTAs pulls
+// items from an atomic counter; items are ordered tile-group-major so the
+// CTAs running at the same time share the same X tiles in L2.  Per item:
+//   1. one thread stages the block's compiled programs into shared memory
+//      with bulk asynchronous copies (cp.async.bulk, completion on an
+//      mbarrier); they stay there for all g tiles;
+//   2. for every tile the CTA loads X (coalesced, transposed to
+//      feature-major [F][tp] so a lane reads its points with 16-byte loads)
+//      and the targets;
+//   3. the warps pull (tree, 32*K-point chunk) sub-items, longest program
+//      first, and run the tree's program over the chunk (K points per lane);
+//   4. MSE mode: each chunk's squared residuals are summed in FP32 per lane
+//      and across the warp with shuffles; chunk sums are folded into FP64
+//      per-tree accumulators in a fixed order, so the result does not depend
+//      on which warp ran which chunk; one FP64 partial per (tree, output,
+//      tile group) goes to the workspace and a finalize kernel sums the
+//      groups in order and divides by D.
+//   Forward mode writes every output point instead.
+#include "tgp_internal.cuh"
+
+namespace tgp {
+
+// ----------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// 1-D bulk copy global -> shared (TMA engine); bytes a multiple of 16, both
+// addresses 16-byte aligned.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Bounded wait on an mbarrier phase: gives up after ~2^22 polls (each poll
+// itself suspends for a while), records the error and reports failure.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned* ctrl) {
+  for (int it = 0; it < (1 << 22); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  atomicOr(&ctrl[CTRL_ERROR], (unsigned)ERR_MBAR_TIMEOUT);
+  // give the copies still in flight a second bounded window to land before
+  // the CTA (and its shared memory) goes away
+  for (int it = 0; it < (1 << 20); ++it)
+    if (mbar_try_wait(bar, parity)) break;
+  return false;
+}
+
+// ----------------------------------------------------------- lane points
+// A lane owns K points of a chunk of 32*K: for K = 8 the points
+// 4*lane + {0..3} and 128 + 4*lane + {0..3}; for K = 4 the points
+// 4*lane + {0..3}.  Both halves are one 16-byte shared-memory load.
+template <int K>
+__device__ __forceinline__ void ld_pts(float (&v)[K], const float* p) {
+  float4 u = *reinterpret_cast<const float4*>(p);
+  v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w;
+  if constexpr (K == 8) {
+    float4 w = *reinterpret_cast<const float4*>(p + 128);
+    v[4] = w.x; v[5] = w.y; v[6] = w.z; v[7] = w.w;
+  }
+}
+template <int K>
+__device__ __forceinline__ void st_pts(float* p, const float (&v)[K]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  if constexpr (K == 8) *reinterpret_cast<float4*>(p + 128) = make_float4(v[4], v[5], v[6], v[7]);
+}
+template <int K>
+__device__ __forceinline__ int pt_index(int lane, int j) {
+  return (j < 4) ? 4 * lane + j : 128 + 4 * lane + (j - 4);
+}
+
+// Modi accumulation: out[o][lane points] += t
+template <int K>
+__device__ __forceinline__ void modi_add(float* mo, int o, const float (&t)[K]) {
+  float* q = mo + o * (32 * K);
+  float v[K];
+  ld_pts<K>(v, q);
+#pragma unroll
+  for (int j = 0; j < K; ++j) v[j] = __fadd_rn(v[j], t[j]);
+  st_pts<K>(q, v);
+}
+
+// ----------------------------------------------------------- interpreter
+// Runs one compiled program over the lane's K points.  xc points at the
+// chunk's first point of feature 0 offset by 4*lane; feature f is at
+// xc + f*xs_stride.  Returns true when the outputs are the Modi sums in mo
+// (else the single output is acc).
+template <int K, bool MODI>
+__device__ __forceinline__ bool run_program(const uint2* __restrict__ pg, const float* __restrict__ xc,
+                                            int xs_stride, float* __restrict__ mo, float (&acc)[K]) {
+  float s[R][K];
+  float L[K], t[K];
+#pragma unroll
+  for (int d = 0; d < R; ++d)
+#pragma unroll
+    for (int j = 0; j < K; ++j) s[d][j] = 0.0f;
+#pragma unroll
+  for (int j = 0; j < K; ++j) acc[j] = 0.0f;
+
+  int pc = 0;
+  uint2 ins = pg[0];
+  for (;;) {
+    const uint2 nxt = pg[pc + 1];
+    ++pc;
+    const uint32_t op = ins.x & 0xFFu;
+    const int o = (int)((ins.x >> 8) & 0xFFu);
+    const float cval = __uint_as_float(ins.y);
+    // feature row of a variable operand (only formed by the *V forms)
+#define XR() (xc + (unsigned)ins.y * (unsigned)xs_stride)
+
+#define TGP_FOR_J _Pragma("unroll") for (int j = 0; j < K; ++j)
+#define LOADV() ld_pts<K>(L, XR())
+#define LOADC() TGP_FOR_J L[j] = cval
+
+    switch (op) {
+      case OP_END_ROOT: return false;
+      case OP_END_MODI: return true;
+      case OP_LDV: ld_pts<K>(acc, XR()); break;
+      case OP_LDC: TGP_FOR_J acc[j] = cval; break;
+
+#define C_UN(F) \
+  case OP_UN + (F - F_SIN): TGP_FOR_J acc[j] = fn1<F>(acc[j]); break; \
+  case OP_UNV + (F - F_SIN): LOADV(); TGP_FOR_J acc[j] = fn1<F>(L[j]); break;
+      C_UN(F_SIN) C_UN(F_COS) C_UN(F_PLOG) C_UN(F_CEXP) C_UN(F_TAN)
+#undef C_UN
+
+#define C_B(F) \
+  case OP_BV + F: LOADV(); TGP_FOR_J acc[j] = fn2<F>(acc[j], L[j]); break; \
+  case OP_BC + F: TGP_FOR_J acc[j] = fn2<F>(acc[j], cval); break; \
+  case OP_RV + F: LOADV(); TGP_FOR_J acc[j] = fn2<F>(L[j], acc[j]); break; \
+  case OP_RC + F: TGP_FOR_J acc[j] = fn2<F>(cval, acc[j]); break;
+      C_B(F_ADD) C_B(F_SUB) C_B(F_MUL) C_B(F_PDIV) C_B(F_MAX)
+#undef C_B
+
+#define C_SP(D) \
+  case OP_SPV + D: TGP_FOR_J s[D][j] = acc[j]; ld_pts<K>(acc, XR()); break; \
+  case OP_SPC + D: TGP_FOR_J { s[D][j] = acc[j]; acc[j] = cval; } break;
+      C_SP(0) C_SP(1) C_SP(2) C_SP(3) C_SP(4) C_SP(5) C_SP(6) C_SP(7)
+#undef C_SP
+
+#define C_S(F, D) \
+  case OP_BS + F * R + D: TGP_FOR_J acc[j] = fn2<F>(s[D][j], acc[j]); break; \
+  case OP_RS + F * R + D: TGP_FOR_J acc[j] = fn2<F>(acc[j], s[D][j]); break;
+#define C_SD(F) C_S(F, 0) C_S(F, 1) C_S(F, 2) C_S(F, 3) C_S(F, 4) C_S(F, 5) C_S(F, 6) C_S(F, 7)
+      C_SD(F_ADD) C_SD(F_SUB) C_SD(F_MUL) C_SD(F_PDIV) C_SD(F_MAX)
+#undef C_SD
+#undef C_S
+
+      default:
+        if constexpr (MODI) {
+          switch (op) {
+#define M_UN(F) \
+  case OP_UN_M + (F - F_SIN): TGP_FOR_J t[j] = fn1<F>(acc[j]); modi_add<K>(mo, o, t); break;
+            M_UN(F_SIN) M_UN(F_COS) M_UN(F_PLOG) M_UN(F_CEXP) M_UN(F_TAN)
+#undef M_UN
+#define M_B(F) \
+  case OP_BV_M + F: LOADV(); TGP_FOR_J { t[j] = fn2<F>(acc[j], L[j]); acc[j] = L[j]; } modi_add<K>(mo, o, t); break; \
+  case OP_BC_M + F: TGP_FOR_J { t[j] = fn2<F>(acc[j], cval); acc[j] = cval; } modi_add<K>(mo, o, t); break; \
+  case OP_RV_M + F: LOADV(); TGP_FOR_J t[j] = fn2<F>(L[j], acc[j]); modi_add<K>(mo, o, t); break; \
+  case OP_RC_M + F: TGP_FOR_J t[j] = fn2<F>(cval, acc[j]); modi_add<K>(mo, o, t); break;
+            M_B(F_ADD) M_B(F_SUB) M_B(F_MUL) M_B(F_PDIV) M_B(F_MAX)
+#undef M_B
+#define M_S(F, D) \
+  case OP_BS_M + F * R + D: TGP_FOR_J t[j] = fn2<F>(s[D][j], acc[j]); modi_add<K>(mo, o, t); break; \
+  case OP_RS_M + F * R + D: TGP_FOR_J { t[j] = fn2<F>(acc[j], s[D][j]); acc[j] = s[D][j]; } modi_add<K>(mo, o, t); break;
+#define M_SD(F) M_S(F, 0) M_S(F, 1) M_S(F, 2) M_S(F, 3) M_S(F, 4) M_S(F, 5) M_S(F, 6) M_S(F, 7)
+            M_SD(F_ADD) M_SD(F_SUB) M_SD(F_MUL) M_SD(F_PDIV) M_SD(F_MAX)
+#undef M_SD
+#undef M_S
+            default: __builtin_unreachable();
+          }
+        } else {
+          __builtin_unreachable();
+        }
+    }
+#undef LOADV
+#undef LOADC
+#undef XR
+#undef TGP_FOR_J
+    ins = nxt;
+  }
+}
+
+// ----------------------------------------------------------- smem layout
+struct EvalSmem {
+  size_t prog, xs, ys, mo, cpart, tacc, order, lens, misc, total;
+  int xs_stride;
+};
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline EvalSmem eval_smem_layout(int K, int nw, bool modi, bool mse, int bt,
+                                                     int pcap, int tp, int F, int O) {
+  EvalSmem L;
+  size_t off = 0;
+  L.prog = off; off = align_up(off + (size_t)bt * pcap * 8, 16);
+  L.xs_stride = tp + 4;
+  L.xs = off; off = align_up(off + (size_t)F * L.xs_stride * 4, 16);
+  L.ys = off; off = align_up(off + (mse ? (size_t)O * tp * 4 : 0), 16);
+  L.mo = off; off = align_up(off + (modi ? (size_t)nw * O * 32 * K * 4 : 0), 16);
+  int cpt = tp / (32 * K);
+  L.cpart = off; off = align_up(off + (size_t)bt * cpt * O * 4, 16);
+  L.tacc = off; off = align_up(off + (size_t)bt * O * 8, 16);
+  L.order = off; off = align_up(off + (size_t)bt * 4, 16);
+  L.lens = off; off = align_up(off + (size_t)bt * 4, 16);
+  L.misc = off; off = align_up(off + 64, 16);
+  L.total = off;
+  return L;
+}
+
+// ----------------------------------------------------------- kernel
+template <int K, int NW, bool MODI, bool OUT>
+__global__ void __launch_bounds__(NW * 32, 2) eval_kernel(EvalArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int CH = 32 * K;
+
+  // Which kernel serves a single-output population depends on whether the
+  // stage pass found a Modi node; the other variant leaves at once.
+  if (a.O == 1) {
+    const bool any_modi = *((volatile unsigned*)&a.ctrl[CTRL_ANY_MODI]) != 0;
+    if (any_modi != MODI) return;
+  }
+
+  const EvalSmem lay = eval_smem_layout(K, NW, MODI, !OUT, a.bt, a.pcap, a.tp, a.F, a.O);
+  uint2* prog_s = reinterpret_cast<uint2*>(smem + lay.prog);
+  float* xs = reinterpret_cast<float*>(smem + lay.xs);
+  float* ys = reinterpret_cast<float*>(smem + lay.ys);
+  float* mo = reinterpret_cast<float*>(smem + lay.mo) + warp * a.O * CH;
+  float* cpart = reinterpret_cast<float*>(smem + lay.cpart);
+  double* tacc = reinterpret_cast<double*>(smem + lay.tacc);
+  int* order = reinterpret_cast<int*>(smem + lay.order);
+  int* lens = reinterpret_cast<int*>(smem + lay.lens);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + lay.misc);
+  long long* s_item = reinterpret_cast<long long*>(smem + lay.misc + 8);
+  int* s_sub = reinterpret_cast<int*>(smem + lay.misc + 16);
+  const int XS = lay.xs_stride;
+  const int cpt = a.tp / CH;
+  const int O = a.O;
+
+  if (tid == 0) {
+    mbar_init(mbar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+
+  for (;;) {
+    if (tid == 0) *s_item = (long long)atomicAdd(&a.ctrl[CTRL_COUNTER], 1u);
+    __syncthreads();
+    const long long item = *s_item;
+    if (item >= a.n_items) break;
+    const int grp = (int)(item / a.n_blocks);
+    const long long blk = item - (long long)grp * a.n_blocks;
+    const long long t0 = blk * a.bt;
+    const int nt = (int)min((long long)a.bt, a.pop - t0);
+
+    // 1. stage the block's programs
+    if (tid == 0) {
+      fence_proxy_async_smem();
+      uint32_t bytes = 0;
+      for (int t = 0; t < nt; ++t) bytes += (uint32_t)((a.plen[t0 + t] + 1) & ~1) * 8u;
+      mbar_arrive_expect_tx(mbar, bytes);
+      for (int t = 0; t < nt; ++t) {
+        int L = a.plen[t0 + t];
+        if (L > 0)
+          bulk_g2s(prog_s + (size_t)t * a.pcap, a.prog + (size_t)(t0 + t) * a.pcap,
+                   (uint32_t)((L + 1) & ~1) * 8u, mbar);
+      }
+    }
+    // longest program first
+    for (int t = tid; t < nt; t += NW * 32) {
+      int Lt = a.plen[t0 + t];
+      int rank = 0;
+      for (int u = 0; u < nt; ++u) {
+        int Lu = a.plen[t0 + u];
+        rank += (Lu > Lt) || (Lu == Lt && u < t);
+      }
+      order[rank] = t;
+      lens[t] = Lt;
+    }
+    if (!OUT)
+      for (int i = tid; i < nt * O; i += NW * 32) tacc[i] = 0.0;
+    if (!mbar_wait_bounded(mbar, phase, a.ctrl)) return;
+    phase ^= 1u;
+    __syncthreads();
+
+    for (int gi = 0; gi < a.g; ++gi) {
+      const long long tile = (long long)grp * a.g + gi;
+      if (tile >= a.n_tiles) break;
+      const long long p0 = tile * a.tp;
+      const int np = (int)min((long long)a.tp, a.D - p0);
+
+      // 2. X tile -> xs[f][q] (zero beyond D), targets -> ys[o][q]
+      {
+        const int fw = min(a.F, 32), rows = 32 / fw, rr = lane / fw, ff = lane - rr * fw;
+        for (int f0 = 0; f0 < a.F; f0 += 32) {
+          const int f = f0 + ff;
+          const bool act = rr < rows && f < a.F;
+#pragma unroll 4
+          for (int r0 = warp * rows; r0 < a.tp; r0 += NW * rows) {
+            const int q = r0 + rr;
+            if (act && q < a.tp) {
+              float v = 0.0f;
+              if (q < np) v = __ldg(a.X + (p0 + q) * a.ldx + f);
+              xs[f * XS + q] = v;
+            }
+          }
+        }
+        if (!OUT) {
+          const int ow = min(O, 32), orows = 32 / ow, orr = lane / ow, off = lane - orr * ow;
+          const bool oact = orr < orows;
+#pragma unroll 4
+          for (int r0 = warp * orows; r0 < a.tp; r0 += NW * orows) {
+            const int q = r0 + orr;
+            if (oact && q < a.tp) {
+              float v = 0.0f;
+              if (q < np) v = __ldg(a.y + (p0 + q) * O + off);
+              ys[off * a.tp + q] = v;
+            }
+          }
+        }
+      }
+      if (tid == 0) *s_sub = 0;
+      __syncthreads();
+
+      // 3. sub-items: (tree, chunk), longest program first
+      const int nch = (np + CH - 1) / CH;
+      const int nsub = nt * nch;
+      for (;;) {
+        int s = 0;
+        if (lane == 0) s = atomicAdd(s_sub, 1);
+        s = __shfl_sync(0xffffffffu, s, 0);
+        if (s >= nsub) break;
+        const int t = order[s / nch];
+        const int ch = s - (s / nch) * nch;
+        const long long p = t0 + t;
+        const int qbase = ch * CH;
+        float res[K];
+        bool modi_out = false;
+        const bool valid = lens[t] > 0;
+        if (valid) {
+          if constexpr (MODI) {
+            float z[K];
+#pragma unroll
+            for (int j = 0; j < K; ++j) z[j] = 0.0f;
+            for (int oo = 0; oo < O; ++oo) st_pts<K>(mo + oo * CH + 4 * lane, z);
+          }
+          modi_out = run_program<K, MODI>(prog_s + (size_t)t * a.pcap, xs + qbase + 4 * lane, XS,
+                                           mo + 4 * lane, res);
+        }
+        for (int oo = 0; oo < O; ++oo) {
+          float v[K];
+          if (!valid) {
+#pragma unroll
+            for (int j = 0; j < K; ++j) v[j] = __int_as_float(0x7fc00000);
+          } else if (MODI && modi_out) {
+            ld_pts<K>(v, mo + oo * CH + 4 * lane);
+          } else {
+#pragma unroll
+            for (int j = 0; j < K; ++j) v[j] = oo == 0 ? res[j] : 0.0f;
+          }
+          if constexpr (OUT) {
+            float* dst = a.out + (p * O + oo) * a.D + p0;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+              const int q = qbase + pt_index<K>(lane, j);
+              if (q < np) dst[q] = v[j];
+            }
+          } else {
+            float yv[K];
+            ld_pts<K>(yv, ys + oo * a.tp + qbase + 4 * lane);
+            float sse = 0.0f;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+              const int q = qbase + pt_index<K>(lane, j);
+              const float r = __fsub_rn(v[j], yv[j]);
+              if (q < np) sse = fmaf(r, r, sse);
+            }
+#pragma unroll
+            for (int m = 16; m > 0; m >>= 1) sse += __shfl_xor_sync(0xffffffffu, sse, m);
+            if (lane == 0) cpart[(t * cpt + ch) * O + oo] = valid ? sse : 0.0f;
+          }
+        }
+      }
+      __syncthreads();
+      // 4. fold chunk sums into the per-tree FP64 accumulators in chunk order
+      if (!OUT) {
+        for (int i = tid; i < nt * O; i += NW * 32) {
+          const int t = i / O, oo = i - (i / O) * O;
+          double acc = tacc[i];
+          for (int ch = 0; ch < nch; ++ch) acc += (double)cpart[(t * cpt + ch) * O + oo];
+          tacc[i] = acc;
+        }
+        __syncthreads();
+      }
+    }
+    if (!OUT) {
+      for (int i = tid; i < nt * O; i += NW * 32) {
+        const int t = i / O, oo = i - (i / O) * O;
+        a.partial[((t0 + t) * O + oo) * a.n_groups + grp] = tacc[i];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// MSE[p,k] = (sum of the tile-group partials in order) / D; NaN for invalid trees.
+__global__ void finalize_kernel(FinalArgs a) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.pop * a.O) return;
+  const long long p = i / a.O;
+  double s = 0.0;
+  const double* src = a.partial + i * a.n_groups;
+  for (int g = 0; g < a.n_groups; ++g) s += src[g];
+  a.mse[i] = a.status[p] != 0 ? __longlong_as_double(0x7ff8000000000000ll) : s / (double)a.D;
+}
+
+// ----------------------------------------------------------- host-side table
+struct EvalKernelInfo {
+  const void* fn;
+  int K, nw;
+  bool modi, out;
+};
+
+#define TGP_EVAL_INST(K, NW, M, O) {(const void*)eval_kernel<K, NW, M, O>, K, NW, M, O}
+static const EvalKernelInfo kEvalKernels[] = {
+    TGP_EVAL_INST(8, 8, false, false), TGP_EVAL_INST(4, 8, false, false),
+    TGP_EVAL_INST(4, 8, true, false),  TGP_EVAL_INST(8, 8, false, true),
+    TGP_EVAL_INST(4, 8, false, true),  TGP_EVAL_INST(4, 8, true, true),
+};
+#undef TGP_EVAL_INST
+
+const void* find_eval_kernel(int K, int nw, bool modi, bool out) {
+  for (const auto& k : kEvalKernels)
+    if (k.K == K && k.nw == nw && k.modi == modi && k.out == out) return k.fn;
+  return nullptr;
+}
+
+size_t eval_smem_bytes(int K, int nw, bool modi, bool mse, int bt, int pcap, int tp, int F, int O) {
+  return eval_smem_layout(K, nw, modi, mse, bt, pcap, tp, F, O).total;
+}
+
+const void* finalize_kernel_ptr() { return (const void*)finalize_kernel; }
+
+}  // namespace tgp

@@ -1,0 +1,268 @@
+// stage.cu -- validation and compilation of the population tensors.
+//
+// One warp per tree.  The lanes read the tree's three rows (Sec. III-A
+// encoding) coalesced, check every node in parallel, and check the subtree
+// sizes locally: a node of arity a at position i with size s is consistent iff
+// its children, found from the sizes (first child at i+1, second at
+// i+1+size[i+1]), tile [i+1, i+s) exactly.  These local rules hold at every
+// position of [0, len) exactly when the arrays encode one tree of len nodes.
+// Lane 0 then compiles the tree into the register-machine program described
+// in tgp_internal.cuh: a bottom-up pass computes how many registers each
+// subtree needs when the hungrier child is evaluated first (Sethi-Ullman
+// numbering), and a stack-free walk over parent links emits the post-order
+// instruction stream with leaves fused into their parents.
+#include "tgp_internal.cuh"
+
+namespace tgp {
+
+// per-warp shared memory: node records of one tree
+struct NodeSmem {
+  uint32_t info[MAX_LEN];   // bits 0-3 func, 4-5 kind (0 var,1 const,2 unary,3 binary), 6 modi, 8-15 out
+  uint32_t leaf[MAX_LEN];   // variable index or constant bits
+  int16_t sz[MAX_LEN];      // subtree size (0 = not a valid size)
+  int16_t par[MAX_LEN];     // parent index
+  uint8_t need[MAX_LEN];    // registers the subtree needs (acc + slots)
+  uint8_t slot[MAX_LEN];    // first free slot when the subtree is evaluated
+};
+
+constexpr int STAGE_WARPS = 4;
+
+__device__ __forceinline__ bool is_int(float v) { return isfinite(v) && v == floorf(v); }
+
+__device__ __forceinline__ int kind_of(uint32_t in) { return (in >> 4) & 3; }
+
+__global__ void __launch_bounds__(STAGE_WARPS * 32) stage_kernel(StageArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  NodeSmem& ns = reinterpret_cast<NodeSmem*>(smem_raw)[warp];
+
+  for (long long p = (long long)blockIdx.x * STAGE_WARPS + warp; p < a.pop;
+       p += (long long)gridDim.x * STAGE_WARPS) {
+    const float* T = a.type + p * a.ld;
+    const float* V = a.val + p * a.ld;
+    const float* S = a.size + p * a.ld;
+    int len = 0;
+    if (lane == 0) {
+      float s0 = S[0];
+      len = (is_int(s0) && s0 >= 1.0f && s0 <= (float)a.max_len) ? (int)s0 : 0;
+    }
+    len = __shfl_sync(0xffffffffu, len, 0);
+    int st = 0;
+    bool modi_here = false;
+    if (len == 0) {
+      st = S_LEN;
+    } else {
+      // ---- per-node checks (lane-parallel)
+      for (int i = lane; i < len; i += 32) {
+        float tv = T[i], vv = V[i], sv = S[i];
+        int ty = is_int(tv) && tv >= 0.0f && tv < 64.0f ? (int)tv : -1;
+        uint32_t info = 0, leaf = 0;
+        int base = ty >= 0 ? (ty & ~T_MODI) : -1;
+        bool modi = ty >= 0 && (ty & T_MODI);
+        if (!(ty == 0 || ty == 1 || ty == 2 || ty == 3 || ty == 18 || ty == 19)) {
+          st |= S_TYPE;
+        } else if (base == T_VAR) {
+          if (!is_int(vv) || vv < 0.0f || vv >= (float)a.n_features) st |= S_VAR;
+          else leaf = (uint32_t)vv;
+          info = 0u << 4;
+        } else if (base == T_CONST) {
+          if (!isfinite(vv)) st |= S_CONST;
+          leaf = __float_as_uint(vv);
+          info = 1u << 4;
+        } else {
+          if (!is_int(vv) || vv < 0.0f || vv >= 65536.0f) {
+            st |= S_FUNC;
+          } else {
+            int iv = (int)vv;
+            int f = iv & 255, o = iv >> 8;
+            if (f >= F_COUNT || arity(f) != (base == T_UFUNC ? 1 : 2)) st |= S_FUNC;
+            if (modi) {
+              if (o >= a.n_outputs) st |= S_MODI;
+            } else if (o != 0) {
+              st |= S_FUNC;
+            }
+            info = (uint32_t)(f & 15) | ((base == T_UFUNC ? 2u : 3u) << 4) | (modi ? 64u : 0u) |
+                   ((uint32_t)(o & 255) << 8);
+            modi_here |= modi;
+          }
+        }
+        ns.info[i] = info;
+        ns.leaf[i] = leaf;
+        ns.sz[i] = (is_int(sv) && sv >= 1.0f && sv <= (float)(len - i)) ? (int16_t)sv : (int16_t)0;
+      }
+      st = __reduce_or_sync(0xffffffffu, st);
+      modi_here = __any_sync(0xffffffffu, modi_here);
+      __syncwarp();
+      if (!(st & (S_TYPE | S_FUNC))) {
+        // ---- local subtree-size rules (lane-parallel)
+        int bad = 0;
+        for (int i = lane; i < len; i += 32) {
+          int s = ns.sz[i];
+          int k = kind_of(ns.info[i]);
+          if (s == 0) { bad = 1; continue; }
+          if (k <= 1) {
+            if (s != 1) bad = 1;
+          } else if (k == 2) {
+            if (s < 2 || ns.sz[i + 1] == 0 || s != 1 + ns.sz[i + 1]) bad = 1;
+            else ns.par[i + 1] = (int16_t)i;
+          } else {
+            if (s < 3) { bad = 1; continue; }
+            int s1 = ns.sz[i + 1];
+            int c2 = i + 1 + s1;
+            if (s1 == 0 || c2 >= i + s) { bad = 1; continue; }
+            int s2 = ns.sz[c2];
+            if (s2 == 0 || s != 1 + s1 + s2) { bad = 1; continue; }
+            ns.par[i + 1] = (int16_t)i;
+            ns.par[c2] = (int16_t)i;
+          }
+        }
+        if (__any_sync(0xffffffffu, bad)) st |= S_SIZE;
+      }
+      __syncwarp();
+    }
+
+    int pc = 0;
+    if (st == 0 && lane == 0) {
+      // ---- registers needed per subtree (bottom-up)
+      for (int i = len - 1; i >= 0; --i) {
+        int k = kind_of(ns.info[i]);
+        int nd;
+        if (k <= 1) {
+          nd = 1;
+        } else if (k == 2) {
+          nd = ns.need[i + 1];
+        } else {
+          int ca = i + 1, cb = ca + ns.sz[ca];
+          bool la = kind_of(ns.info[ca]) <= 1, lb = kind_of(ns.info[cb]) <= 1;
+          if (lb) nd = ns.need[ca];
+          else if (la) nd = ns.need[cb];
+          else {
+            int na = ns.need[ca], nb = ns.need[cb];
+            nd = na >= nb ? max(na, nb + 1) : max(nb, na + 1);
+          }
+        }
+        ns.need[i] = (uint8_t)min(nd, 255);
+      }
+      // ---- post-order walk over parent links, leaves fused into parents
+      uint2* prog = a.prog + p * a.pcap;
+      int n = 0, pend = -1, last_ldv = -1;
+      bool down = true, deep = false;
+      ns.slot[0] = 0;
+      for (;;) {
+        uint32_t in = ns.info[n];
+        int k = kind_of(in);
+        if (down) {
+          int c = -1;
+          if (k == 2) {
+            c = n + 1;
+          } else if (k == 3) {
+            int ca = n + 1, cb = ca + ns.sz[ca];
+            bool la = kind_of(ns.info[ca]) <= 1, lb = kind_of(ns.info[cb]) <= 1;
+            c = lb ? ca : la ? cb : (ns.need[ca] >= ns.need[cb] ? ca : cb);
+          }
+          if (c < 0) {  // a leaf evaluated on its own: load it (spilling acc first if pending)
+            uint2 ins;
+            bool var = k == 0;
+            if (pend >= 0) {
+              ins.x = (var ? OP_SPV : OP_SPC) + pend;
+              pend = -1;
+              last_ldv = -1;
+            } else {
+              ins.x = var ? OP_LDV : OP_LDC;
+              last_ldv = var ? pc : -1;
+            }
+            ins.y = ns.leaf[n];
+            prog[pc++] = ins;
+            down = false;
+          } else {
+            ns.slot[c] = ns.slot[n];
+            n = c;
+          }
+          continue;
+        }
+        if (n == 0) break;
+        int q = ns.par[n];
+        uint32_t qin = ns.info[q];
+        int qk = kind_of(qin);
+        int ca = q + 1, cb = ca + ns.sz[ca];
+        bool la = false, lb = false, a_first = true;
+        if (qk == 3) {
+          la = kind_of(ns.info[ca]) <= 1;
+          lb = kind_of(ns.info[cb]) <= 1;
+          a_first = ns.need[ca] >= ns.need[cb];
+          if (!la && !lb) {
+            int second = a_first ? cb : ca;
+            if (n != second) {  // first child done: spill it, evaluate the other one
+              pend = ns.slot[q];
+              if (pend >= R) { deep = true; break; }
+              ns.slot[second] = ns.slot[q] + 1;
+              n = second;
+              down = true;
+              continue;
+            }
+          }
+        }
+        // ---- emit the instruction of node q
+        int f = qin & 15;
+        bool modi = qin & 64;
+        uint32_t o8 = ((qin >> 8) & 255) << 8;
+        uint2 ins;
+        ins.y = 0;
+        if (qk == 2) {
+          if (modi) {
+            ins.x = (OP_UN_M + (f - F_SIN)) | o8;
+          } else if (last_ldv == pc - 1 && last_ldv >= 0) {
+            ins.x = OP_UNV + (f - F_SIN);  // fuse with the variable load just emitted
+            ins.y = prog[pc - 1].y;
+            --pc;
+          } else {
+            ins.x = OP_UN + (f - F_SIN);
+          }
+        } else if (lb) {
+          bool var = kind_of(ns.info[cb]) == 0;
+          ins.x = (modi ? (var ? OP_BV_M : OP_BC_M) : (var ? OP_BV : OP_BC)) + f;
+          ins.x |= modi ? o8 : 0;
+          ins.y = ns.leaf[cb];
+        } else if (la) {
+          bool var = kind_of(ns.info[ca]) == 0;
+          if (modi) ins.x = ((var ? OP_RV_M : OP_RC_M) + f) | o8;
+          else if (f == F_ADD || f == F_MUL) ins.x = (var ? OP_BV : OP_BC) + f;
+          else ins.x = (var ? OP_RV : OP_RC) + f;
+          ins.y = ns.leaf[ca];
+        } else {
+          int d = ns.slot[q];
+          if (d >= R) { deep = true; break; }
+          uint32_t base = a_first ? (modi ? OP_BS_M : OP_BS) : (modi ? OP_RS_M : OP_RS);
+          ins.x = (base + f * R + d) | (modi ? o8 : 0);
+        }
+        prog[pc++] = ins;
+        last_ldv = -1;
+        n = q;
+      }
+      if (deep) {
+        st = S_DEPTH;
+        pc = 0;
+      } else {
+        uint2 end;
+        end.x = (a.n_outputs == 1 && !modi_here) ? OP_END_ROOT : OP_END_MODI;
+        end.y = 0;
+        prog[pc++] = end;
+      }
+    }
+    st = __shfl_sync(0xffffffffu, st, 0);
+    pc = __shfl_sync(0xffffffffu, pc, 0);
+    if (lane == 0) {
+      a.status[p] = st;
+      if (a.user_status) a.user_status[p] = st;
+      a.plen[p] = st == 0 ? pc : 0;
+      if (st == 0 && modi_here) atomicOr(&a.ctrl[CTRL_ANY_MODI], 1u);
+    }
+    __syncwarp();
+  }
+}
+
+size_t stage_smem_bytes() { return sizeof(NodeSmem) * STAGE_WARPS; }
+int stage_threads() { return STAGE_WARPS * 32; }
+const void* stage_kernel_ptr() { return (const void*)stage_kernel; }
+
+}  // namespace tgp

@@ -1,0 +1,217 @@
+// tgp_internal.cuh -- shared definitions of the sm_103a kernels: the compiled
+// instruction set, the FP32 function table, workspace layout and kernel
+// argument blocks.
+//
+// Evaluation model.  The paper evaluates a prefix tree with a value stack,
+// walking the nodes from the end to the start (Sec. III-C).  Here each tree is
+// first compiled (stage kernel) into a register-machine program for a warp:
+//   * one warp evaluates one tree over 32*K data points (K points per lane);
+//     every lane runs the same instruction, so dispatch never diverges;
+//   * the top of the stack is held in registers ("acc", K values per lane),
+//     the rest in R = 8 register slots s[0..7] addressed only by instruction
+//     variants with a compile-time slot number, so nothing spills to memory;
+//   * operands are evaluated in Sethi-Ullman order (the child that needs more
+//     slots first), which bounds the slots by log2(leaves) + 1: eight slots
+//     cover every binary/unary tree of up to 1023 nodes;
+//   * leaves are fused into their parent's instruction (a variable operand is
+//     read from the shared-memory tile of X, a constant rides in the
+//     instruction word), so leaves cost no dispatch of their own;
+//   * a Modi node (Sec. IV-C) is one instruction that adds its function value
+//     into its output accumulator and leaves its rightmost child's value in
+//     acc for the parent.
+// Reordering the operand evaluation does not change any value: every
+// function is pure, only the order in which Modi contributions are summed
+// into an output changes.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tgp {
+
+// ------------------------------------------------------------- encoding
+enum NodeType : int { T_VAR = 0, T_CONST = 1, T_UFUNC = 2, T_BFUNC = 3, T_MODI = 16 };
+enum Func : int { F_ADD = 0, F_SUB, F_MUL, F_PDIV, F_MAX, F_SIN, F_COS, F_PLOG, F_CEXP, F_TAN, F_COUNT };
+enum TreeStatus : int {
+  S_LEN = 1, S_TYPE = 2, S_FUNC = 4, S_VAR = 8, S_MODI = 16, S_CONST = 32, S_SIZE = 64, S_DEPTH = 128
+};
+
+constexpr int R = 8;            // register slots below the accumulator
+constexpr int MAX_LEN = 1024;   // longest supported tree
+constexpr int MAX_OUT = 16;     // outputs
+constexpr int MAX_FEAT = 256;   // features
+
+// ------------------------------------------------------------- instruction set
+// One instruction is a uint2: .x = opcode | out_index << 8; .y = the leaf
+// operand (feature index for *V forms, float bits of the constant for *C
+// forms, slot-free forms ignore it).  f = function id 0..9, d = slot 0..7.
+enum Op : uint32_t {
+  OP_END_ROOT = 0,   // output 0 := acc (single output, no Modi node)
+  OP_END_MODI = 1,   // outputs are the Modi accumulators
+  OP_LDV = 2,        // acc = x[v]
+  OP_LDC = 3,        // acc = c
+  OP_UN = 4,         // + (f-5):   acc = f(acc)                       4..8
+  OP_UNV = 9,        // + (f-5):   acc = f(x[v])                      9..13
+  OP_BV = 14,        // + f:       acc = f(acc, x[v])                14..18
+  OP_BC = 19,        // + f:       acc = f(acc, c)                   19..23
+  OP_RV = 24,        // + f:       acc = f(x[v], acc)                24..28
+  OP_RC = 29,        // + f:       acc = f(c, acc)                   29..33
+  OP_UN_M = 34,      // + (f-5):   out[o] += f(acc)                  34..38
+  OP_BV_M = 39,      // + f:       out[o] += f(acc, x[v]); acc = x[v]
+  OP_BC_M = 44,      // + f:       out[o] += f(acc, c);    acc = c
+  OP_RV_M = 49,      // + f:       out[o] += f(x[v], acc)
+  OP_RC_M = 54,      // + f:       out[o] += f(c, acc)               54..58
+  OP_SPV = 59,       // + d:       s[d] = acc; acc = x[v]            59..66
+  OP_SPC = 67,       // + d:       s[d] = acc; acc = c               67..74
+  OP_BS = 75,        // + f*R + d: acc = f(s[d], acc)                75..114
+  OP_RS = 115,       // + f*R + d: acc = f(acc, s[d])               115..154
+  OP_BS_M = 155,     // + f*R + d: out[o] += f(s[d], acc)           155..194
+  OP_RS_M = 195,     // + f*R + d: out[o] += f(acc, s[d]); acc = s[d]  195..234
+  OP_COUNT = 235
+};
+
+__host__ __device__ constexpr int arity(int f) { return f <= F_MAX ? 2 : 1; }
+
+// ------------------------------------------------------------- FP32 functions
+// Guards and clamp of the protected operators (library reading of the paper's
+// protected division, log and exp).
+#define TGP_GUARD 1e-6f
+#define TGP_EXP_CLAMP 80.0f
+
+__device__ __forceinline__ float mufu_sin(float x) {
+  float y;
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float mufu_cos(float x) {
+  float y;
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float mufu_ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float mufu_lg2(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float mufu_rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Two-constant Cody-Waite reduction of x to r = x - k*2pi, |r| <= pi
+// (W. J. Cody and W. Waite, Software Manual for the Elementary Functions,
+// 1980).  2pi = C1 + C2 with C1 = 6.28125 (8 significant bits, so k*C1 is
+// exact for |k| < 2^16) and C2 = 2pi - 6.28125 rounded to float.
+__device__ __forceinline__ float reduce_2pi(float x) {
+  const float inv_2pi = 0.15915494f;  // 1/(2pi) rounded to float
+  const float c1 = 6.28125f;
+  const float c2 = 1.9353072e-3f;     // (2pi - 6.28125) rounded to float
+  float k = rintf(__fmul_rn(x, inv_2pi));
+  float r = fmaf(-k, c1, x);
+  return fmaf(-k, c2, r);
+}
+
+// Binary function f(a, b); the first prefix child is a.
+template <int F>
+__device__ __forceinline__ float fn2(float a, float b) {
+  if constexpr (F == F_ADD) return __fadd_rn(a, b);
+  else if constexpr (F == F_SUB) return __fsub_rn(a, b);
+  else if constexpr (F == F_MUL) return __fmul_rn(a, b);
+  else if constexpr (F == F_PDIV) return fabsf(b) > TGP_GUARD ? __fmul_rn(a, mufu_rcp(b)) : 1.0f;
+  else return fmaxf(a, b);
+}
+
+// Unary function f(a).
+template <int F>
+__device__ __forceinline__ float fn1(float a) {
+  if constexpr (F == F_SIN) return mufu_sin(reduce_2pi(a));
+  else if constexpr (F == F_COS) return mufu_cos(reduce_2pi(a));
+  else if constexpr (F == F_PLOG)
+    return fabsf(a) > TGP_GUARD ? __fmul_rn(mufu_lg2(fabsf(a)), 0.6931472f) : 0.0f;  // ln 2
+  else if constexpr (F == F_CEXP)
+    return mufu_ex2(__fmul_rn(fminf(a, TGP_EXP_CLAMP), 1.442695f));                 // log2 e
+  else {
+    float r = reduce_2pi(a);
+    return __fmul_rn(mufu_sin(r), mufu_rcp(mufu_cos(r)));
+  }
+}
+
+// ------------------------------------------------------------- workspace
+// All regions are 256-byte aligned offsets from the workspace base.
+struct WsLayout {
+  size_t prog;      // uint2 [pop, pcap]  compiled programs
+  size_t plen;      // int32 [pop]        instruction count (0 = invalid tree)
+  size_t status;    // int32 [pop]        per-tree status
+  size_t partial;   // double [pop, n_out, n_groups]  per-item partial SSE
+  size_t ctrl;      // uint32 [64]: [0] work counter, [1] any-Modi flag, [2] error word
+  size_t total;
+  int pcap;         // instructions per program slot (even)
+  int n_groups;     // partial sums per tree and output
+};
+
+// Launch shape after the heuristic.
+struct Shape {
+  int K;         // points per lane
+  int nw;        // warps per CTA
+  int bt;        // trees per block
+  int tp;        // points per tile
+  int g;         // tiles per item
+  int n_tiles;
+  int n_groups;
+  int n_blocks;
+  long long n_items;
+};
+
+struct StageArgs {
+  const float* type;
+  const float* val;
+  const float* size;
+  long long pop, ld;
+  int max_len, n_features, n_outputs;
+  uint2* prog;
+  int pcap;
+  int* plen;
+  int* status;
+  int* user_status;   // may be null
+  unsigned* ctrl;
+};
+
+struct EvalArgs {
+  const uint2* prog;
+  const int* plen;
+  const int* status;
+  int pcap;
+  long long pop;
+  const float* X;
+  long long D;
+  int F;
+  long long ldx;
+  const float* y;     // [D, O] (MSE mode)
+  int O;
+  float* out;         // [pop, O, D] (forward mode)
+  double* partial;    // [pop, O, n_groups] (MSE mode)
+  int bt, tp, g, n_tiles, n_groups, n_blocks;
+  long long n_items;
+  unsigned* ctrl;
+};
+
+struct FinalArgs {
+  const double* partial;
+  const int* status;
+  double* mse;
+  long long pop;
+  int O, n_groups;
+  long long D;
+};
+
+// control word indices
+enum { CTRL_COUNTER = 0, CTRL_ANY_MODI = 1, CTRL_ERROR = 2, CTRL_WORDS = 64 };
+// bits of the error word
+enum { ERR_MBAR_TIMEOUT = 1 };
+
+}  // namespace tgp

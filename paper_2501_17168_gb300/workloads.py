@@ -147,14 +147,15 @@ def encode(tokens, ld: int | None = None) -> Population:
             v[i] = f + 256 * (out or 0)
             ar.append(ARITY[f])
 
-    def walk(i):
-        j = i + 1
-        for _ in range(ar[i]):
-            j = walk(j)
-        s[i] = j - i
-        return j
-
-    if walk(0) != n:
+    # subtree sizes from the arities, right to left with a stack of sizes
+    stk = []
+    for i in range(n - 1, -1, -1):
+        if len(stk) < ar[i]:
+            raise ValueError("tokens do not form exactly one prefix tree")
+        kids = [stk.pop() for _ in range(ar[i])]
+        s[i] = 1 + sum(kids)
+        stk.append(int(s[i]))
+    if len(stk) != 1:
         raise ValueError("tokens do not form exactly one prefix tree")
     return Population(t[None], v[None], s[None], ld)
 
