@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Benchmark: population-wide SR fitness (forward + MSE) on one GB300.
+
+One step = one pass of the fitness hot path over one population: validate
+and compile the trees, evaluate every tree on every data point, reduce the
+squared residuals to a per-tree MSE.  Workload (default): 5,000 random trees
+of length <= 255 (depth <= 8), 16 float32 features N(0,1), 100,000 points,
+targets from a length-31 ground-truth tree plus N(0, 0.01^2) noise.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` is node-point evaluations per second
+(GPops/s with one generation, Sec. V-C) over the whole job with inputs
+resident in HBM; `e2e` is the same metric through the C ABI from pinned host
+buffers with the copies inside the timed region; `roofline` relates the
+evaluation kernel to the FP32/SFU issue and HBM roofline; `cpu_baseline` is
+the FP64 oracle on the host cores on a bounded sample of the same workload.
+`--impl reference` times that oracle as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "node·point evals/sec and % roofline for population MSE fitness; fwd+bwd time"
+UNIT = "node·point evals/s"
+L2_FLUSH_BYTES = 256 << 20
+
+# Algorithmic instruction counts per node-point (one lane-op each) and SFU
+# cost in SM cycles per lane-op: sin, cos, lg2 and rcp issue at 16 lanes per
+# SM per clock on GB300, ex2 (ftz) at 32 (measured).  Leaves cost nothing.
+FP32_OPS = {0: 1, 1: 1, 2: 1, 3: 2, 4: 1, 5: 1, 6: 1, 7: 2, 8: 2, 9: 2}
+SFU_CYC = {3: 1 / 16, 5: 1 / 16, 6: 1 / 16, 7: 1 / 16, 8: 1 / 32, 9: 3 / 16}
+MSE_FP32_PER_POINT = 2
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sr_scale", choices=["sr_scale"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--pop", type=int, default=5000, help="trees (smaller cases for profiling)")
+    ap.add_argument("--points", type=int, default=100_000, help="data points")
+    return ap.parse_args()
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+def _workload_desc(prob):
+    return (f"{prob.name}: {prob.pop.pop} random trees, length<=255 (depth<=8), "
+            f"{prob.F} float32 features N(0,1), {prob.D} points, y = GT(len 31) + N(0,0.01^2); "
+            f"forward + MSE")
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- helpers
+def _src_hash():
+    h = hashlib.sha256()
+    for f in ("eval.cu", "tgp_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2501_17168_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _profile_traffic(workload):
+    """DRAM bytes per launch of the evaluation kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", f"eval_kernel_{workload}.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
+    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m or not t or m.group(1) != _src_hash():
+        return None
+    return float(t.group(1))
+
+
+def _roofline_time(pop, D, sms, f_hz, hbm_gbs, n_outputs=1):
+    """FP32-issue and SFU-issue times of one evaluation pass at the given clock."""
+    n_fp32 = 0.0
+    n_sfu = 0.0
+    t, v = pop.type, pop.val
+    L = pop.lengths()
+    mask = np.arange(pop.ld)[None, :] < L[:, None]
+    fn = mask & ((t == 2) | (t == 3) | (t == 18) | (t == 19))
+    ids, counts = np.unique(np.mod(v[fn].astype(np.int64), 256), return_counts=True)
+    for f, c in zip(ids, counts):
+        n_fp32 += FP32_OPS[int(f)] * c * D
+        n_sfu += SFU_CYC.get(int(f), 0.0) * c * D
+    n_fp32 += MSE_FP32_PER_POINT * pop.pop * n_outputs * D
+    t_fp32 = n_fp32 / (sms * 128 * f_hz)
+    t_sfu = n_sfu / (sms * f_hz)
+    return t_fp32, t_sfu
+
+
+def _bytes_once(pop, D, F, n_outputs=1):
+    return 4.0 * D * F + 4.0 * D * n_outputs + 12.0 * pop.pop * pop.ld + 8.0 * pop.pop * n_outputs
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(a, rank, world):
+    import oracle
+    from paper_2501_17168_gb300 import workloads as W
+    if rank != 0:
+        return 0
+    prob = W.sr_scale(0, pop=a.pop, D=a.points)
+    cores = os.cpu_count() or 1
+    # bounded sample: every 50th tree over all points (about 1e9 node-points)
+    pick = np.arange(0, prob.pop.pop, 50)
+    sub = prob.pop.take(pick)
+    gt, _ = oracle.evaluate(prob.gt.type, prob.gt.val, prob.gt.size, prob.X, threads=cores)
+    y = (gt[0, 0] + prob.noise[:, 0]).astype(np.float32)
+    units = float(sub.nodes()) * prob.D
+    for _ in range(a.warmup):
+        oracle.mse(sub.type, sub.val, sub.size, prob.X, y, threads=cores)
+    times = []
+    for _ in range(a.steps):
+        t0 = time.perf_counter()
+        oracle.mse(sub.type, sub.val, sub.size, prob.X, y, threads=cores)
+        times.append(time.perf_counter() - t0)
+    T = sum(times)
+    value = units * a.steps / T
+    sample = f"every 50th tree ({sub.pop} trees, {sub.nodes()} nodes) x all {prob.D} points"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * T / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": _workload_desc(prob), "pop": prob.pop.pop,
+                                        "n_points": prob.D, "n_features": prob.F},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- our arm
+def cpu_baseline(prob, seconds_target=15.0):
+    import oracle
+    cores = os.cpu_count() or 1
+    gt, _ = oracle.evaluate(prob.gt.type, prob.gt.val, prob.gt.size, prob.X, threads=cores)
+    y = (gt[0, 0] + prob.noise[:, 0]).astype(np.float32)
+    # calibrate on a small slice, then time a sample of about seconds_target
+    pick = np.arange(0, prob.pop.pop, 500)
+    sub = prob.pop.take(pick)
+    t0 = time.perf_counter()
+    oracle.mse(sub.type, sub.val, sub.size, prob.X, y, threads=cores)
+    rate = sub.nodes() * prob.D / max(time.perf_counter() - t0, 1e-6)
+    n_trees = int(min(prob.pop.pop, max(cores, rate * seconds_target / (prob.pop.nodes() / prob.pop.pop * prob.D))))
+    stride = max(1, prob.pop.pop // n_trees)
+    sub = prob.pop.take(np.arange(0, prob.pop.pop, stride))
+    t0 = time.perf_counter()
+    oracle.mse(sub.type, sub.val, sub.size, prob.X, y, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": sub.nodes() * prob.D / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"every {stride}th tree ({sub.pop} trees, {sub.nodes()} nodes) x all {prob.D} "
+                      f"points, {dt:.1f} s wall"}
+
+
+def run_ours(a, rank, world, local_rank):
+    import torch
+    from paper_2501_17168_gb300 import api, build, workloads as W
+    build.build_all()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    prob = W.sr_scale(rank, pop=a.pop, D=a.points)
+    t, v, s = api.population_to(prob.pop, dev)
+    X = torch.from_numpy(prob.X).to(dev)
+    # targets: ground-truth tree evaluated by the library, plus noise
+    gt_t, gt_v, gt_s = api.population_to(prob.gt, dev)
+    gy, _ = api.tgp_eval_forward(gt_t, gt_v, gt_s, X, 1, max_len=prob.gt.max_len)
+    y = (gy[0, 0] + torch.from_numpy(prob.noise[:, 0]).to(dev)).contiguous().view(-1, 1)
+    P, D, F = prob.pop.pop, prob.D, prob.F
+    mse = torch.empty((P, 1), dtype=torch.float64, device=dev)
+    st = torch.empty(P, dtype=torch.int32, device=dev)
+    units = float(prob.pop.nodes()) * D
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step(cfg=None):
+        api.tgp_fitness_mse(t, v, s, X, y, 1, max_len=prob.pop.max_len, config=cfg, mse=mse,
+                            tree_status=st)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    api.tgp_check_device_error(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(a.steps)]
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        time.sleep(0.3)
+        for i in range(a.steps):
+            flush.zero_()  # L2 flush outside the timed events
+            ev[i][0].record()
+            step({"eval_begin_event": ev[i][2], "eval_end_event": ev[i][3]})
+            ev[i][1].record()
+        torch.cuda.synchronize()
+    api.tgp_check_device_error(dev)
+    step_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    eval_ms = [e[2].elapsed_time(e[3]) for e in ev]
+    T = sum(step_ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([T], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        T = float(tt.item())
+    total_units = units * a.steps * world
+    value = total_units / T
+    assert (st.cpu().numpy() == 0).all()
+
+    result = None
+    if rank == 0:
+        hbm_gbs, sm_max_mhz, peak_kind = _peaks()
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        f_hz = sm_max_mhz * 1e6
+        t_fp32, t_sfu = _roofline_time(prob.pop, D, sms, f_hz, hbm_gbs)
+        nbytes = _bytes_once(prob.pop, D, F)
+        t_mem = nbytes / (hbm_gbs * 1e9)
+        t_roof = max(t_fp32, t_sfu, t_mem)
+        term = {t_fp32: "fp32", t_sfu: "sfu", t_mem: "hbm"}[t_roof]
+        eval_s = statistics.mean(eval_ms) / 1e3
+        achieved = units / eval_s
+        peak = units / t_roof
+        clocks = clk.summary()
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1e3 * T / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": _workload_desc(prob), "pop": P, "max_len": prob.pop.max_len,
+                       "n_points": D, "n_features": F, "nodes": prob.pop.nodes(),
+                       "node_points_per_step": units,
+                       "l2": "flushed between steps (256 MiB write outside the timed events)",
+                       "parallelism": f"population replicas x{world}" if world > 1 else "1 GPU"},
+            "roofline": {"bound": "alu", "term": term, "achieved": achieved / 1e9,
+                         "peak": peak / 1e9, "unit": "Gnode·pt/s", "frac": achieved / peak,
+                         "traffic": _profile_traffic(a.workload),
+                         "kernel": "eval_kernel<8,8,plain,mse>",
+                         "kernel_ms": 1e3 * eval_s,
+                         "peak_basis": f"{sms} SMs x (FP32 128 / SFU 16 (ex2 32) lanes per clock) at "
+                                       f"{sm_max_mhz:.0f} MHz, HBM {hbm_gbs} GB/s ({peak_kind})",
+                         "t_fp32_ms": 1e3 * t_fp32, "t_sfu_ms": 1e3 * t_sfu, "t_hbm_ms": 1e3 * t_mem,
+                         "frac_at_sampled_clock": (achieved / peak) * (sm_max_mhz / clocks["sm_mhz"])
+                         if clocks.get("sm_mhz") else None},
+            "gpu_launches": 4 * a.steps,
+            "clocks": clocks,
+        }
+        if not a.no_e2e:
+            result["e2e"] = e2e(prob, dev, a, units)
+        if not a.no_cpu_baseline and world == 1:
+            result["cpu_baseline"] = cpu_baseline(prob)
+    return result
+
+
+def e2e(prob, dev, a, units):
+    """Same metric through the C ABI from pinned host buffers: H2D copies of
+    the population, X and y, the fitness call, D2H of MSE and status."""
+    import torch
+    from paper_2501_17168_gb300 import api
+    pin = lambda arr: torch.from_numpy(np.ascontiguousarray(arr)).pin_memory()
+    ht, hv, hs, hX = pin(prob.pop.type), pin(prob.pop.val), pin(prob.pop.size), pin(prob.X)
+    dt_, dv_, ds_ = (torch.empty_like(x, device=dev) for x in (ht, hv, hs))
+    dX = torch.empty_like(hX, device=dev)
+    gt_t, gt_v, gt_s = api.population_to(prob.gt, dev)
+    X0 = hX.to(dev)
+    gy, _ = api.tgp_eval_forward(gt_t, gt_v, gt_s, X0, 1, max_len=prob.gt.max_len)
+    hy = (gy[0, 0].cpu() + torch.from_numpy(prob.noise[:, 0])).contiguous().view(-1, 1).pin_memory()
+    dy = torch.empty_like(hy, device=dev)
+    P = prob.pop.pop
+    hm = torch.empty((P, 1), dtype=torch.float64).pin_memory()
+    hst = torch.empty(P, dtype=torch.int32).pin_memory()
+    dm = torch.empty((P, 1), dtype=torch.float64, device=dev)
+    dst = torch.empty(P, dtype=torch.int32, device=dev)
+
+    def step():
+        for d, h in ((dt_, ht), (dv_, hv), (ds_, hs), (dX, hX), (dy, hy)):
+            d.copy_(h, non_blocking=True)
+        api.tgp_fitness_mse(dt_, dv_, ds_, dX, dy, 1, max_len=prob.pop.max_len, mse=dm, tree_status=dst)
+        hm.copy_(dm, non_blocking=True)
+        hst.copy_(dst, non_blocking=True)
+
+    for _ in range(max(a.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    T = e0.elapsed_time(e1) / 1e3
+    h2d = sum(x.numel() * x.element_size() for x in (ht, hv, hs, hX, hy))
+    d2h = hm.numel() * 8 + hst.numel() * 4
+    return {"value": units * a.steps / T, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * T / a.steps}
+
+
+def main():
+    a = _args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        return run_reference(a, rank, world)
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    res = run_ours(a, rank, world, local_rank)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

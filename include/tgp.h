@@ -111,6 +111,9 @@ typedef struct tgp_config {
                                32 * points_per_lane (up to 4096)              */
   int32_t tiles_per_item;   /* consecutive tiles one work item sweeps         */
   int32_t points_per_lane;  /* 4 or 8 points evaluated per thread             */
+  void* eval_begin_event;   /* optional cudaEvent_t recorded on the stream just
+                               before the evaluation kernel(s), NULL = none  */
+  void* eval_end_event;     /* optional cudaEvent_t recorded just after them  */
 } tgp_config;
 
 /* Bytes of workspace the calls below need for these arguments (0 on invalid

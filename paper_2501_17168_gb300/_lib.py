@@ -33,7 +33,8 @@ class tgp_data(ctypes.Structure):
 
 class tgp_config(ctypes.Structure):
     _fields_ = [("trees_per_block", ctypes.c_int32), ("points_per_tile", ctypes.c_int32),
-                ("tiles_per_item", ctypes.c_int32), ("points_per_lane", ctypes.c_int32)]
+                ("tiles_per_item", ctypes.c_int32), ("points_per_lane", ctypes.c_int32),
+                ("eval_begin_event", ctypes.c_void_p), ("eval_end_event", ctypes.c_void_p)]
 
 
 _P = ctypes.POINTER

@@ -43,10 +43,14 @@ def _f32(t: torch.Tensor, name: str) -> torch.Tensor:
 def make_population(type_, val, size, max_len: int | None = None) -> tgp_population:
     for name, t in (("type", type_), ("value", val), ("size", size)):
         _f32(t, name)
-        if t.dim() != 2 or t.stride(1) != 1:
-            raise ValueError(f"{name} must be [pop, ld] with unit column stride")
-    if not (type_.shape == val.shape == size.shape and type_.stride() == val.stride() == size.stride()):
-        raise ValueError("type, value and size must share shape and strides")
+        if t.dim() != 2:
+            raise ValueError(f"{name} must be [pop, ld]")
+        if t.numel() > 0 and t.shape[1] > 1 and t.stride(1) != 1:
+            raise ValueError(f"{name} must have unit column stride")
+    if not type_.shape == val.shape == size.shape:
+        raise ValueError("type, value and size must share their shape")
+    if type_.numel() > 0 and not type_.stride() == val.stride() == size.stride():
+        raise ValueError("type, value and size must share their strides")
     P, L = type_.shape
     ld = type_.stride(0) if P > 1 else L
     return tgp_population(type_.data_ptr(), val.data_ptr(), size.data_ptr(), P,
@@ -69,8 +73,14 @@ def make_config(cfg) -> tgp_config | None:
         return None
     if isinstance(cfg, tgp_config):
         return cfg
+    ev0, ev1 = cfg.get("eval_begin_event"), cfg.get("eval_end_event")
+    for ev in (ev0, ev1):
+        if ev is not None and not ev.cuda_event:
+            ev.record()  # torch creates the CUDA event lazily on its first record
     return tgp_config(int(cfg.get("trees_per_block", 0)), int(cfg.get("points_per_tile", 0)),
-                      int(cfg.get("tiles_per_item", 0)), int(cfg.get("points_per_lane", 0)))
+                      int(cfg.get("tiles_per_item", 0)), int(cfg.get("points_per_lane", 0)),
+                      ev0.cuda_event if ev0 is not None else None,
+                      ev1.cuda_event if ev1 is not None else None)
 
 
 def _cref(c):

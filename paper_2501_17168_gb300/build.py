@@ -50,8 +50,17 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def generate(force: bool = False):
+    """Regenerates the inline-PTX interpreter headers when their generator changed."""
+    gen = os.path.join(CSRC, "gen_interp.py")
+    out = os.path.join(CSRC, "interp_fwd.cuh")
+    if force or _stale(out, [gen]):
+        subprocess.check_call([sys.executable, gen])
+
+
 def build_library(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
     os.makedirs(BUILD, exist_ok=True)
+    generate()
     srcs = _sources()
     headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(INCLUDE, "tgp.h")]
     if not force and not _stale(LIB, _deps()):

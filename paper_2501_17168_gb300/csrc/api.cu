@@ -268,8 +268,14 @@ tgp_status run(const tgp_population* pop, const tgp_data* data, const float* y, 
   sm.g = (int)cdiv(sm.n_tiles, n_groups);
   sp.n_items = (long long)sp.n_blocks * n_groups;
   sm.n_items = (long long)sm.n_blocks * n_groups;
+  if (cfg && cfg->eval_begin_event &&
+      cudaEventRecord(reinterpret_cast<cudaEvent_t>(cfg->eval_begin_event), st) != cudaSuccess)
+    return TGP_ERR_CUDA;
   s = launch_eval(pop, data, y, O, out, w, wsb, sp, sm, st, dv, mse);
   if (s != TGP_OK) return s;
+  if (cfg && cfg->eval_end_event &&
+      cudaEventRecord(reinterpret_cast<cudaEvent_t>(cfg->eval_end_event), st) != cudaSuccess)
+    return TGP_ERR_CUDA;
   if (mse) {
     FinalArgs f;
     f.partial = reinterpret_cast<const double*>(wsb + w.partial);

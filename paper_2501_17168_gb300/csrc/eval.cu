@@ -20,6 +20,7 @@
 //      groups in order and divides by D.
 //   Forward mode writes every output point instead.
 #include "tgp_internal.cuh"
+#include "interp_fwd.cuh"
 
 namespace tgp {
 
@@ -94,118 +95,6 @@ __device__ __forceinline__ void st_pts(float* p, const float (&v)[K]) {
 template <int K>
 __device__ __forceinline__ int pt_index(int lane, int j) {
   return (j < 4) ? 4 * lane + j : 128 + 4 * lane + (j - 4);
-}
-
-// Modi accumulation: out[o][lane points] += t
-template <int K>
-__device__ __forceinline__ void modi_add(float* mo, int o, const float (&t)[K]) {
-  float* q = mo + o * (32 * K);
-  float v[K];
-  ld_pts<K>(v, q);
-#pragma unroll
-  for (int j = 0; j < K; ++j) v[j] = __fadd_rn(v[j], t[j]);
-  st_pts<K>(q, v);
-}
-
-// ----------------------------------------------------------- interpreter
-// Runs one compiled program over the lane's K points.  xc points at the
-// chunk's first point of feature 0 offset by 4*lane; feature f is at
-// xc + f*xs_stride.  Returns true when the outputs are the Modi sums in mo
-// (else the single output is acc).
-template <int K, bool MODI>
-__device__ __forceinline__ bool run_program(const uint2* __restrict__ pg, const float* __restrict__ xc,
-                                            int xs_stride, float* __restrict__ mo, float (&acc)[K]) {
-  float s[R][K];
-  float L[K], t[K];
-#pragma unroll
-  for (int d = 0; d < R; ++d)
-#pragma unroll
-    for (int j = 0; j < K; ++j) s[d][j] = 0.0f;
-#pragma unroll
-  for (int j = 0; j < K; ++j) acc[j] = 0.0f;
-
-  int pc = 0;
-  uint2 ins = pg[0];
-  for (;;) {
-    const uint2 nxt = pg[pc + 1];
-    ++pc;
-    const uint32_t op = ins.x & 0xFFu;
-    const int o = (int)((ins.x >> 8) & 0xFFu);
-    const float cval = __uint_as_float(ins.y);
-    // feature row of a variable operand (only formed by the *V forms)
-#define XR() (xc + (unsigned)ins.y * (unsigned)xs_stride)
-
-#define TGP_FOR_J _Pragma("unroll") for (int j = 0; j < K; ++j)
-#define LOADV() ld_pts<K>(L, XR())
-#define LOADC() TGP_FOR_J L[j] = cval
-
-    switch (op) {
-      case OP_END_ROOT: return false;
-      case OP_END_MODI: return true;
-      case OP_LDV: ld_pts<K>(acc, XR()); break;
-      case OP_LDC: TGP_FOR_J acc[j] = cval; break;
-
-#define C_UN(F) \
-  case OP_UN + (F - F_SIN): TGP_FOR_J acc[j] = fn1<F>(acc[j]); break; \
-  case OP_UNV + (F - F_SIN): LOADV(); TGP_FOR_J acc[j] = fn1<F>(L[j]); break;
-      C_UN(F_SIN) C_UN(F_COS) C_UN(F_PLOG) C_UN(F_CEXP) C_UN(F_TAN)
-#undef C_UN
-
-#define C_B(F) \
-  case OP_BV + F: LOADV(); TGP_FOR_J acc[j] = fn2<F>(acc[j], L[j]); break; \
-  case OP_BC + F: TGP_FOR_J acc[j] = fn2<F>(acc[j], cval); break; \
-  case OP_RV + F: LOADV(); TGP_FOR_J acc[j] = fn2<F>(L[j], acc[j]); break; \
-  case OP_RC + F: TGP_FOR_J acc[j] = fn2<F>(cval, acc[j]); break;
-      C_B(F_ADD) C_B(F_SUB) C_B(F_MUL) C_B(F_PDIV) C_B(F_MAX)
-#undef C_B
-
-#define C_SP(D) \
-  case OP_SPV + D: TGP_FOR_J s[D][j] = acc[j]; ld_pts<K>(acc, XR()); break; \
-  case OP_SPC + D: TGP_FOR_J { s[D][j] = acc[j]; acc[j] = cval; } break;
-      C_SP(0) C_SP(1) C_SP(2) C_SP(3) C_SP(4) C_SP(5) C_SP(6) C_SP(7)
-#undef C_SP
-
-#define C_S(F, D) \
-  case OP_BS + F * R + D: TGP_FOR_J acc[j] = fn2<F>(s[D][j], acc[j]); break; \
-  case OP_RS + F * R + D: TGP_FOR_J acc[j] = fn2<F>(acc[j], s[D][j]); break;
-#define C_SD(F) C_S(F, 0) C_S(F, 1) C_S(F, 2) C_S(F, 3) C_S(F, 4) C_S(F, 5) C_S(F, 6) C_S(F, 7)
-      C_SD(F_ADD) C_SD(F_SUB) C_SD(F_MUL) C_SD(F_PDIV) C_SD(F_MAX)
-#undef C_SD
-#undef C_S
-
-      default:
-        if constexpr (MODI) {
-          switch (op) {
-#define M_UN(F) \
-  case OP_UN_M + (F - F_SIN): TGP_FOR_J t[j] = fn1<F>(acc[j]); modi_add<K>(mo, o, t); break;
-            M_UN(F_SIN) M_UN(F_COS) M_UN(F_PLOG) M_UN(F_CEXP) M_UN(F_TAN)
-#undef M_UN
-#define M_B(F) \
-  case OP_BV_M + F: LOADV(); TGP_FOR_J { t[j] = fn2<F>(acc[j], L[j]); acc[j] = L[j]; } modi_add<K>(mo, o, t); break; \
-  case OP_BC_M + F: TGP_FOR_J { t[j] = fn2<F>(acc[j], cval); acc[j] = cval; } modi_add<K>(mo, o, t); break; \
-  case OP_RV_M + F: LOADV(); TGP_FOR_J t[j] = fn2<F>(L[j], acc[j]); modi_add<K>(mo, o, t); break; \
-  case OP_RC_M + F: TGP_FOR_J t[j] = fn2<F>(cval, acc[j]); modi_add<K>(mo, o, t); break;
-            M_B(F_ADD) M_B(F_SUB) M_B(F_MUL) M_B(F_PDIV) M_B(F_MAX)
-#undef M_B
-#define M_S(F, D) \
-  case OP_BS_M + F * R + D: TGP_FOR_J t[j] = fn2<F>(s[D][j], acc[j]); modi_add<K>(mo, o, t); break; \
-  case OP_RS_M + F * R + D: TGP_FOR_J { t[j] = fn2<F>(acc[j], s[D][j]); acc[j] = s[D][j]; } modi_add<K>(mo, o, t); break;
-#define M_SD(F) M_S(F, 0) M_S(F, 1) M_S(F, 2) M_S(F, 3) M_S(F, 4) M_S(F, 5) M_S(F, 6) M_S(F, 7)
-            M_SD(F_ADD) M_SD(F_SUB) M_SD(F_MUL) M_SD(F_PDIV) M_SD(F_MAX)
-#undef M_SD
-#undef M_S
-            default: __builtin_unreachable();
-          }
-        } else {
-          __builtin_unreachable();
-        }
-    }
-#undef LOADV
-#undef LOADC
-#undef XR
-#undef TGP_FOR_J
-    ins = nxt;
-  }
 }
 
 // ----------------------------------------------------------- smem layout
@@ -373,8 +262,9 @@ __global__ void __launch_bounds__(NW * 32, 2) eval_kernel(EvalArgs a) {
             for (int j = 0; j < K; ++j) z[j] = 0.0f;
             for (int oo = 0; oo < O; ++oo) st_pts<K>(mo + oo * CH + 4 * lane, z);
           }
-          modi_out = run_program<K, MODI>(prog_s + (size_t)t * a.pcap, xs + qbase + 4 * lane, XS,
-                                           mo + 4 * lane, res);
+          modi_out = interp_fwd<K, MODI>(smem_u32(prog_s + (size_t)t * a.pcap),
+                                          smem_u32(xs + qbase + 4 * lane), (unsigned)XS * 4u,
+                                          smem_u32(mo + 4 * lane), res) != 0;
         }
         for (int oo = 0; oo < O; ++oo) {
           float v[K];

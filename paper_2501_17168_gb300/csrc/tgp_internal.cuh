@@ -72,74 +72,9 @@ enum Op : uint32_t {
 __host__ __device__ constexpr int arity(int f) { return f <= F_MAX ? 2 : 1; }
 
 // ------------------------------------------------------------- FP32 functions
-// Guards and clamp of the protected operators (library reading of the paper's
-// protected division, log and exp).
-#define TGP_GUARD 1e-6f
-#define TGP_EXP_CLAMP 80.0f
-
-__device__ __forceinline__ float mufu_sin(float x) {
-  float y;
-  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float mufu_cos(float x) {
-  float y;
-  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float mufu_ex2(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float mufu_lg2(float x) {
-  float y;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float mufu_rcp(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-// Two-constant Cody-Waite reduction of x to r = x - k*2pi, |r| <= pi
-// (W. J. Cody and W. Waite, Software Manual for the Elementary Functions,
-// 1980).  2pi = C1 + C2 with C1 = 6.28125 (8 significant bits, so k*C1 is
-// exact for |k| < 2^16) and C2 = 2pi - 6.28125 rounded to float.
-__device__ __forceinline__ float reduce_2pi(float x) {
-  const float inv_2pi = 0.15915494f;  // 1/(2pi) rounded to float
-  const float c1 = 6.28125f;
-  const float c2 = 1.9353072e-3f;     // (2pi - 6.28125) rounded to float
-  float k = rintf(__fmul_rn(x, inv_2pi));
-  float r = fmaf(-k, c1, x);
-  return fmaf(-k, c2, r);
-}
-
-// Binary function f(a, b); the first prefix child is a.
-template <int F>
-__device__ __forceinline__ float fn2(float a, float b) {
-  if constexpr (F == F_ADD) return __fadd_rn(a, b);
-  else if constexpr (F == F_SUB) return __fsub_rn(a, b);
-  else if constexpr (F == F_MUL) return __fmul_rn(a, b);
-  else if constexpr (F == F_PDIV) return fabsf(b) > TGP_GUARD ? __fmul_rn(a, mufu_rcp(b)) : 1.0f;
-  else return fmaxf(a, b);
-}
-
-// Unary function f(a).
-template <int F>
-__device__ __forceinline__ float fn1(float a) {
-  if constexpr (F == F_SIN) return mufu_sin(reduce_2pi(a));
-  else if constexpr (F == F_COS) return mufu_cos(reduce_2pi(a));
-  else if constexpr (F == F_PLOG)
-    return fabsf(a) > TGP_GUARD ? __fmul_rn(mufu_lg2(fabsf(a)), 0.6931472f) : 0.0f;  // ln 2
-  else if constexpr (F == F_CEXP)
-    return mufu_ex2(__fmul_rn(fminf(a, TGP_EXP_CLAMP), 1.442695f));                 // log2 e
-  else {
-    float r = reduce_2pi(a);
-    return __fmul_rn(mufu_sin(r), mufu_rcp(mufu_cos(r)));
-  }
-}
+// The function bodies (protected division and log with the 1e-6f guard,
+// exp clamped at 80, sin/cos with a two-constant Cody-Waite reduction on the
+// MUFU approximations) live in the generated interpreter, gen_interp.py.
 
 // ------------------------------------------------------------- workspace
 // All regions are 256-byte aligned offsets from the workspace base.
