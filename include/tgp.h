@@ -145,6 +145,34 @@ tgp_status tgp_fitness_mse_cfg(const tgp_population* pop, const tgp_data* data, 
                                int32_t n_outputs, double* mse, int32_t* tree_status, void* ws,
                                size_t ws_bytes, void* stream, const tgp_config* cfg);
 
+/* Largest scratch tgp_fitness_mse_noalloc can use (32 MiB). */
+#define TGP_NOALLOC_WS_BYTES (32u << 20)
+
+/* tgp_fitness_mse for callers that cannot allocate device memory.  The paper
+ * has no counterpart; this is a deployment convenience of the library.
+ * Some callers have no way to obtain a device buffer for the workspace: a
+ * plain C host that links only this library and the CUDA runtime but owns no
+ * device allocator, a plugin whose host application manages all device
+ * memory itself, or a latency-bound loop that must not call cudaMalloc (which
+ * can synchronize the device).  This entry point takes the same arguments as
+ * tgp_fitness_mse minus ws/ws_bytes and returns the same results; its scratch
+ * is a fixed array of TGP_NOALLOC_WS_BYTES in the library's own device memory
+ * (one per GPU that loads the library, held until the process exits).  It
+ * calls no cudaMalloc, cudaFree or allocating library routine.
+ *   - TGP_ERR_WORKSPACE when the problem needs more scratch than
+ *     TGP_NOALLOC_WS_BYTES (tgp_workspace_size with cfg = NULL tells);
+ *     nothing is launched then.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before capturing a stream.
+ *   - Every call uses the same array and leaves its contents there; the
+ *     words that must start at zero are cleared by each call.  Calls whose
+ *     work can overlap on the GPU (unordered streams, or several host threads)
+ *     race on the array and give wrong results: order them on one stream. */
+tgp_status tgp_fitness_mse_noalloc(const tgp_population* pop, const tgp_data* data,
+                                   const float* y, int32_t n_outputs, double* mse,
+                                   int32_t* tree_status, void* stream);
+
 /* Reads and clears the device error word left in ws by the last calls on
  * this workspace (a bounded wait that gave up).  Synchronizes `stream`.
  * Returns TGP_OK or TGP_ERR_TIMEOUT. */

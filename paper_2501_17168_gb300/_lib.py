@@ -19,6 +19,7 @@ TGP_OK, TGP_ERR_INVALID_ARG, TGP_ERR_INVALID_TREE, TGP_ERR_WORKSPACE, TGP_ERR_CU
 TREE_LEN, TREE_TYPE, TREE_FUNC, TREE_VAR, TREE_MODI, TREE_CONST, TREE_SIZE, TREE_DEPTH = \
     1, 2, 4, 8, 16, 32, 64, 128
 MAX_LEN, MAX_OUTPUTS, MAX_FEATURES = 1024, 16, 256
+NOALLOC_WS_BYTES = 32 << 20
 
 
 class tgp_population(ctypes.Structure):
@@ -61,6 +62,9 @@ _SIGS = {
                                            ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
                                            _P(tgp_config)]),
+    "tgp_fitness_mse_noalloc": (ctypes.c_int, [_P(tgp_population), _P(tgp_data), ctypes.c_void_p,
+                                               ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_void_p]),
     "tgp_check_device_error": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "tgp_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "tgp_version": (ctypes.c_char_p, []),
