@@ -129,7 +129,7 @@ class ClockSampler:
 # ----------------------------------------------------------------- helpers
 def _src_hash():
     h = hashlib.sha256()
-    for f in ("eval.cu", "tgp_internal.cuh"):
+    for f in ("eval.cu", "tgp_internal.cuh", "interp_fwd.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2501_17168_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
