@@ -145,6 +145,27 @@ tgp_status tgp_fitness_mse_cfg(const tgp_population* pop, const tgp_data* data, 
                                int32_t n_outputs, double* mse, int32_t* tree_status, void* ws,
                                size_t ws_bytes, void* stream, const tgp_config* cfg);
 
+/* Reverse-mode gradient of L = sum_{p,k} grad_mse[p,k] * MSE[p,k] (the
+ * adjoint is not in the paper; it differentiates the Sec. III-C fitness).
+ *   grad_mse   [device] double [pop, n_outputs]  upstream gradient
+ *   mse_out    [device] double [pop, n_outputs]  MSE of the same pass, or NULL
+ *              (then trees whose grad_mse row is zero are skipped)
+ *   grad_value [device] float  [pop, ld] or NULL: dL/d(constant) at constant
+ *              nodes, 0 at every other and every padding position, NaN rows
+ *              for invalid trees
+ *   grad_X     [device] float  [n_points, n_features] (contiguous) or NULL:
+ *              dL/dX is ADDED to it (zero it first), so calls accumulate.
+ * Derivative conventions: max sends the gradient to the operand fmax
+ * returned (the left one on a tie); the guard branches of pdiv and plog and
+ * the clamp of cexp have zero derivative.  Intermediate values are recomputed
+ * per point tile (a per-thread tape of at most one value per node), never
+ * stored per population x length x points.  Sums of gradients use atomic
+ * additions, so their last bits may differ between runs. */
+tgp_status tgp_eval_backward(const tgp_population* pop, const tgp_data* data, const float* y,
+                             int32_t n_outputs, const double* grad_mse, double* mse_out,
+                             float* grad_value, float* grad_X, int32_t* tree_status, void* ws,
+                             size_t ws_bytes, void* stream);
+
 /* Largest scratch tgp_fitness_mse_noalloc can use (32 MiB). */
 #define TGP_NOALLOC_WS_BYTES (32u << 20)
 

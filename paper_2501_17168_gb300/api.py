@@ -171,3 +171,43 @@ def tgp_check_device_error(device=None):
 def population_to(pop, device) -> tuple:
     """workloads.Population -> (type, value, size) float32 device tensors."""
     return tuple(torch.from_numpy(a).to(device) for a in (pop.type, pop.val, pop.size))
+
+
+def tgp_eval_backward(type_, val, size, X, y, grad_mse, n_outputs: int = 1, max_len=None,
+                      want_mse: bool = True, want_grad_value: bool = True, want_grad_X: bool = True,
+                      grad_X=None, tree_status=None):
+    """Reverse-mode gradient of sum(grad_mse * MSE).
+
+    Returns (mse [pop, O] float64 or None, grad_value [pop, ld] float32 or None,
+    grad_X [n_points, n_features] float32 or None, tree status).  grad_X, when
+    given, is accumulated into; otherwise a zeroed tensor is allocated.
+    """
+    lib = _lib.load()
+    pop = make_population(type_, val, size, max_len)
+    data = make_data(X)
+    _f32(y, "y")
+    if not y.is_contiguous() or y.numel() != data.n_points * n_outputs:
+        raise ValueError("y must be a contiguous [n_points, n_outputs] float32 tensor")
+    dev = X.device
+    g = grad_mse.to(device=dev, dtype=torch.float64).contiguous()
+    if g.numel() != pop.pop * n_outputs:
+        raise ValueError("grad_mse must have pop * n_outputs elements")
+    mse = torch.empty((pop.pop, n_outputs), dtype=torch.float64, device=dev) if want_mse else None
+    gv = torch.empty(type_.shape, dtype=torch.float32, device=dev) if want_grad_value else None
+    if want_grad_X and grad_X is None:
+        grad_X = torch.zeros(X.shape, dtype=torch.float32, device=dev)
+    if not want_grad_X:
+        grad_X = None
+    if grad_X is not None and (grad_X.shape != X.shape or not grad_X.is_contiguous()):
+        raise ValueError("grad_X must be a contiguous tensor shaped like X")
+    if tree_status is None:
+        tree_status = torch.empty(pop.pop, dtype=torch.int32, device=dev)
+    n = lib.tgp_workspace_size(ctypes.byref(pop), ctypes.byref(data), n_outputs, None)
+    if n == 0:
+        raise _lib.TGPError(_lib.TGP_ERR_INVALID_ARG, "tgp_workspace_size")
+    ws = workspace(n, dev)
+    ptr = lambda t: t.data_ptr() if t is not None else None
+    check(lib.tgp_eval_backward(ctypes.byref(pop), ctypes.byref(data), y.data_ptr(), n_outputs,
+                                g.data_ptr(), ptr(mse), ptr(gv), ptr(grad_X), tree_status.data_ptr(),
+                                ws.data_ptr(), ws.numel(), _stream_handle(dev)), "tgp_eval_backward")
+    return mse, gv, grad_X, tree_status

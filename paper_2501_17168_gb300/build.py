@@ -53,9 +53,11 @@ def _stale(target, deps):
 def generate(force: bool = False):
     """Regenerates the inline-PTX interpreter headers when their generator changed."""
     gen = os.path.join(CSRC, "gen_interp.py")
-    out = os.path.join(CSRC, "interp_fwd.cuh")
-    if force or _stale(out, [gen]):
-        subprocess.check_call([sys.executable, gen])
+    gen_b = os.path.join(CSRC, "gen_interp_bwd.py")
+    if force or _stale(os.path.join(CSRC, "interp_fwd.cuh"), [gen]):
+        subprocess.check_call([sys.executable, gen], cwd=CSRC)
+    if force or _stale(os.path.join(CSRC, "interp_bwd.cuh"), [gen, gen_b]):
+        subprocess.check_call([sys.executable, gen_b], cwd=CSRC)
 
 
 def build_library(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:

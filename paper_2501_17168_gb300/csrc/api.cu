@@ -15,6 +15,9 @@ const void* stage_kernel_ptr();
 const void* find_eval_kernel(int K, int nw, bool modi, bool out);
 size_t eval_smem_bytes(int K, int nw, bool modi, bool mse, int bt, int pcap, int tp, int F, int O);
 const void* finalize_kernel_ptr();
+const void* find_adj_kernel(int K, int nw, bool modi, int max_len, int* cap_out);
+size_t adj_smem_bytes(int K, int nw, bool modi, int pcap, int max_len, int tp, int F, int O);
+const void* adj_finalize_ptr();
 
 namespace {
 
@@ -134,6 +137,8 @@ WsLayout ws_layout(long long P, int max_len, int O, int n_groups) {
   w.plen = off; off = al256(off + (size_t)P * 4);
   w.status = off; off = al256(off + (size_t)P * 4);
   w.partial = off; off = al256(off + (size_t)P * O * n_groups * 8);
+  w.gval64 = off; off = al256(off + (size_t)P * max_len * 8);
+  w.mse64 = off; off = al256(off + (size_t)P * O * 8);
   w.total = off;
   return w;
 }
@@ -294,6 +299,94 @@ tgp_status run(const tgp_population* pop, const tgp_data* data, const float* y, 
   return TGP_OK;
 }
 
+// Fused forward + reverse sweep: one CTA per point tile over all trees.
+tgp_status run_backward(const tgp_population* pop, const tgp_data* data, const float* y, int O,
+                        const double* grad_mse, double* mse_out, float* grad_value, float* grad_X,
+                        int32_t* tree_status, void* ws, size_t ws_bytes, void* stream) {
+  if (!pop_ok(pop) || !data_ok(data) || O < 1 || O > TGP_MAX_OUTPUTS) return TGP_ERR_INVALID_ARG;
+  if (data->n_points < 1) return TGP_ERR_INVALID_ARG;
+  if (pop->pop > 0 && (!y || !grad_mse)) return TGP_ERR_INVALID_ARG;
+  DevInfo dv;
+  if (!dev_info(&dv)) return TGP_ERR_CUDA;
+  Shape sp, sm;
+  if (!shapes_for(pop, data, O, nullptr, true, dv, &sp, &sm)) return TGP_ERR_UNSUPPORTED;
+  const int n_groups = sm.n_groups > sp.n_groups ? sm.n_groups : sp.n_groups;
+  WsLayout w = ws_layout(pop->pop, pop->max_len, O, n_groups);
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < w.total) return TGP_ERR_WORKSPACE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* wsb = reinterpret_cast<char*>(ws);
+  if (cudaMemsetAsync(wsb + w.ctrl, 0, CTRL_WORDS * 4, st) != cudaSuccess) return TGP_ERR_CUDA;
+  if (pop->pop == 0) return TGP_OK;
+  if (cudaMemsetAsync(wsb + w.gval64, 0, w.mse64 + (size_t)pop->pop * O * 8 - w.gval64, st) != cudaSuccess)
+    return TGP_ERR_CUDA;
+  tgp_status s = launch_stage(pop, data->n_features, O, w, wsb, tree_status, st, dv);
+  if (s != TGP_OK) return s;
+  const int K = 4, nw = 8;
+  for (int variant = 0; variant < 2; ++variant) {
+    const bool modi = variant == 1;
+    if (!modi && O > 1) continue;
+    int cap = 0;
+    const void* fn = find_adj_kernel(K, nw, modi, pop->max_len, &cap);
+    if (!fn) return TGP_ERR_UNSUPPORTED;
+    int tp = 512;
+    while (tp > 32 * K && (long long)(tp / 2) >= data->n_points) tp /= 2;
+    size_t smem = adj_smem_bytes(K, nw, modi, w.pcap, pop->max_len, tp, data->n_features, O);
+    while (smem > (size_t)dv.smem_optin && tp > 32 * K) {
+      tp /= 2;
+      smem = adj_smem_bytes(K, nw, modi, w.pcap, pop->max_len, tp, data->n_features, O);
+    }
+    if (smem > (size_t)dv.smem_optin) return TGP_ERR_UNSUPPORTED;
+    if (!ensure_smem(fn, smem)) return TGP_ERR_CUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nw * 32, smem) != cudaSuccess)
+      return TGP_ERR_CUDA;
+    if (per_sm < 1) return TGP_ERR_UNSUPPORTED;
+    AdjArgs a;
+    a.prog = reinterpret_cast<const uint2*>(wsb + w.prog);
+    a.plen = reinterpret_cast<const int*>(wsb + w.plen);
+    a.status = reinterpret_cast<const int*>(wsb + w.status);
+    a.pcap = w.pcap;
+    a.pop = pop->pop;
+    a.max_len = pop->max_len;
+    a.X = data->X;
+    a.D = data->n_points;
+    a.F = data->n_features;
+    a.ldx = data->ldx;
+    a.y = y;
+    a.O = O;
+    a.g = grad_mse;
+    a.want_mse = mse_out != nullptr;
+    a.gval64 = reinterpret_cast<double*>(wsb + w.gval64);
+    a.mse64 = reinterpret_cast<double*>(wsb + w.mse64);
+    a.grad_X = grad_X;
+    a.tp = tp;
+    a.n_tiles = (int)cdiv(data->n_points, tp);
+    a.ctrl = reinterpret_cast<unsigned*>(wsb + w.ctrl);
+    long long grid = (long long)dv.sms * per_sm;
+    if (grid > a.n_tiles) grid = a.n_tiles;
+    void* args[] = {&a};
+    if (cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(nw * 32), args, smem, st) != cudaSuccess)
+      return TGP_ERR_CUDA;
+  }
+  AdjFinalArgs f;
+  f.gval64 = reinterpret_cast<const double*>(wsb + w.gval64);
+  f.mse64 = reinterpret_cast<const double*>(wsb + w.mse64);
+  f.status = reinterpret_cast<const int*>(wsb + w.status);
+  f.grad_value = grad_value;
+  f.mse = mse_out;
+  f.pop = pop->pop;
+  f.ld = pop->ld;
+  f.max_len = pop->max_len;
+  f.O = O;
+  f.D = data->n_points;
+  long long n = pop->pop * (pop->ld > O ? pop->ld : O);
+  void* args[] = {&f};
+  if (cudaLaunchKernel(adj_finalize_ptr(), dim3((unsigned)cdiv(n, 256)), dim3(256), args, 0, st) !=
+      cudaSuccess)
+    return TGP_ERR_CUDA;
+  return TGP_OK;
+}
+
 }  // namespace
 }  // namespace tgp
 
@@ -356,6 +449,14 @@ tgp_status tgp_fitness_mse(const tgp_population* pop, const tgp_data* data, cons
                            int32_t n_outputs, double* mse, int32_t* tree_status, void* ws,
                            size_t ws_bytes, void* stream) {
   return tgp_fitness_mse_cfg(pop, data, y, n_outputs, mse, tree_status, ws, ws_bytes, stream, nullptr);
+}
+
+tgp_status tgp_eval_backward(const tgp_population* pop, const tgp_data* data, const float* y,
+                             int32_t n_outputs, const double* grad_mse, double* mse_out,
+                             float* grad_value, float* grad_X, int32_t* tree_status, void* ws,
+                             size_t ws_bytes, void* stream) {
+  return run_backward(pop, data, y, n_outputs, grad_mse, mse_out, grad_value, grad_X, tree_status, ws,
+                      ws_bytes, stream);
 }
 
 tgp_status tgp_check_device_error(void* ws, size_t ws_bytes, void* stream) {

@@ -1,0 +1,693 @@
+"""Generates interp_bwd.cuh: the two inline-PTX loops of the adjoint kernel.
+
+bwd_forward<K, MODI>  runs a compiled program like the forward interpreter
+                      and, per instruction, appends the local partials the
+                      reverse sweep will need to a per-thread tape in local
+                      memory (at most one entry per tree node):
+                        unary f          f'(a)            (1 entry)
+                        leaf-binary      mul/pdiv/max: the accumulator operand (1)
+                        slot-binary      mul/pdiv/max: both operands (2)
+                        add/sub, leaves  nothing
+bwd_reverse<K, MODI>  walks the program from its last instruction to its
+                      first with the adjoint of the accumulator in registers
+                      (G, K points per lane) and of the eight slots (GS), the
+                      mirror image of the forward register machine: a slot
+                      written by a spill in the forward is read back by that
+                      spill's reverse, after the reverse of its consumer has
+                      stored the slot's adjoint there.  Variable leaves add
+                      their adjoint into the CTA's shared-memory gradient tile
+                      of X (red.shared.add); constant leaves add the
+                      warp-summed adjoint into a per-warp shared array
+                      indexed by the leaf's node position.
+Local derivatives (ties of max go to the operand fmax returned, left on a
+tie; the guards of pdiv and plog and the clamp of cexp give zero
+derivatives on their constant branches):
+  add (1, 1)   sub (1, -1)   mul (b, a)   pdiv (1/b, -a/b^2)
+  sin cos(a)   cos -sin(a)   plog 1/a   cexp exp(a) (a <= 80)   tan 1 + tan^2
+Modi nodes (Sec. IV-C): the function value's adjoint is the seed of its
+output; the value handed to the parent (the rightmost child) keeps the
+parent's adjoint.
+"""
+from __future__ import annotations
+
+import os
+
+from gen_interp import (BIN, C1, C2, CLAMP, F_ADD, F_CEXP, F_COS, F_MAX, F_MUL, F_PDIV, F_PLOG,
+                        F_SIN, F_SUB, F_TAN, GUARD, INV2PI, LN2, LOG2E, MAGIC, ONE, OP_BC, OP_BC_M,
+                        OP_BS, OP_BS_M, OP_BV, OP_BV_M, OP_COUNT, OP_END_MODI, OP_END_ROOT, OP_LDC,
+                        OP_LDV, OP_RC, OP_RC_M, OP_RS, OP_RS_M, OP_RV, OP_RV_M, OP_SPC, OP_SPV, OP_UN,
+                        OP_UN_M, OP_UNV, R, UNA, ZERO, fhex)
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+OUT = os.path.join(HERE, "interp_bwd.cuh")
+
+NEEDS_OPERAND = (F_MUL, F_PDIV, F_MAX)
+
+
+class Base:
+    def __init__(self, K: int, modi: bool):
+        assert K in (4, 8)
+        self.K = K
+        self.modi = modi
+        self.lines: list[str] = []
+
+    def e(self, s):
+        self.lines.append(s)
+
+    def vec(self, p, n=None):
+        return lambda j: f"{p}{j}"
+
+    def load_x(self, dst):
+        self.e("mad.lo.u32 r_ad, r_iy, r_xstr, r_xc;")
+        self.e(f"ld.shared.v4.f32 {{{dst(0)}, {dst(1)}, {dst(2)}, {dst(3)}}}, [r_ad];")
+        if self.K == 8:
+            self.e(f"ld.shared.v4.f32 {{{dst(4)}, {dst(5)}, {dst(6)}, {dst(7)}}}, [r_ad+512];")
+
+    def tape_put(self, src):
+        for h in range(self.K // 4):
+            regs = ", ".join(src(4 * h + q) for q in range(4))
+            self.e(f"st.local.v4.f32 [r_tape+{16 * h}], {{{regs}}};")
+        self.e(f"add.u32 r_tape, r_tape, {4 * self.K};")
+
+    def tape_get(self, dst):
+        self.e(f"sub.u32 r_tape, r_tape, {4 * self.K};")
+        for h in range(self.K // 4):
+            regs = ", ".join(dst(4 * h + q) for q in range(4))
+            self.e(f"ld.local.v4.f32 {{{regs}}}, [r_tape+{16 * h}];")
+
+    def reduce(self, j, x):
+        self.e(f"mul.rn.f32 W{j}, {x}, {INV2PI};")
+        self.e(f"add.rn.f32 W{j}, W{j}, {MAGIC};")
+        self.e(f"sub.rn.f32 W{j}, {MAGIC}, W{j};")
+        self.e(f"fma.rn.f32 V{j}, W{j}, {C1}, {x};")
+        self.e(f"fma.rn.f32 V{j}, W{j}, {C2}, V{j};")
+
+    def fn2(self, f, out, a, b):
+        for j in range(self.K):
+            o, x, y = out(j), a(j), b(j)
+            if f == F_ADD:
+                self.e(f"add.rn.f32 {o}, {x}, {y};")
+            elif f == F_SUB:
+                self.e(f"sub.rn.f32 {o}, {x}, {y};")
+            elif f == F_MUL:
+                self.e(f"mul.rn.f32 {o}, {x}, {y};")
+            elif f == F_MAX:
+                self.e(f"max.f32 {o}, {x}, {y};")
+            elif f == F_PDIV:
+                self.e(f"abs.f32 V{j}, {y};")
+                self.e(f"setp.gt.f32 P{j}, V{j}, {GUARD};")
+                self.e(f"rcp.approx.ftz.f32 V{j}, {y};")
+                self.e(f"mul.rn.f32 V{j}, {x}, V{j};")
+                self.e(f"selp.f32 {o}, V{j}, {ONE}, P{j};")
+
+    def fn1d(self, f, out, a, d):
+        """out[j] = f(a[j]) and d[j] = f'(a[j]) (d computed before out is written)."""
+        for j in range(self.K):
+            o, x, dd = out(j), a(j), d(j)
+            if f in (F_SIN, F_COS, F_TAN):
+                self.reduce(j, x)
+                if f == F_SIN:
+                    self.e(f"cos.approx.ftz.f32 {dd}, V{j};")
+                    self.e(f"sin.approx.ftz.f32 {o}, V{j};")
+                elif f == F_COS:
+                    self.e(f"sin.approx.ftz.f32 {dd}, V{j};")
+                    self.e(f"neg.f32 {dd}, {dd};")
+                    self.e(f"cos.approx.ftz.f32 {o}, V{j};")
+                else:
+                    self.e(f"cos.approx.ftz.f32 W{j}, V{j};")
+                    self.e(f"sin.approx.ftz.f32 V{j}, V{j};")
+                    self.e(f"rcp.approx.ftz.f32 W{j}, W{j};")
+                    self.e(f"mul.rn.f32 {o}, V{j}, W{j};")
+                    self.e(f"fma.rn.f32 {dd}, {o}, {o}, {ONE};")
+            elif f == F_PLOG:
+                self.e(f"abs.f32 V{j}, {x};")
+                self.e(f"setp.gt.f32 P{j}, V{j}, {GUARD};")
+                self.e(f"rcp.approx.ftz.f32 W{j}, {x};")
+                self.e(f"selp.f32 {dd}, W{j}, {ZERO}, P{j};")
+                self.e(f"lg2.approx.ftz.f32 V{j}, V{j};")
+                self.e(f"mul.rn.f32 V{j}, V{j}, {LN2};")
+                self.e(f"selp.f32 {o}, V{j}, {ZERO}, P{j};")
+            elif f == F_CEXP:
+                self.e(f"setp.le.f32 P{j}, {x}, {CLAMP};")
+                self.e(f"min.f32 V{j}, {x}, {CLAMP};")
+                self.e(f"mul.rn.f32 V{j}, V{j}, {LOG2E};")
+                self.e(f"ex2.approx.ftz.f32 {o}, V{j};")
+                self.e(f"selp.f32 {dd}, {o}, {ZERO}, P{j};")
+
+    def modi_add(self, src):
+        self.e("bfe.u32 r_moo, r_ix, 8, 8;")
+        self.e(f"mad.lo.u32 r_ma, r_moo, {128 * self.K}, r_mo;")
+        for h in range(self.K // 4):
+            regs = [f"M{4 * h + q}" for q in range(4)]
+            off = f"+{512 * h}" if h else ""
+            self.e(f"ld.shared.v4.f32 {{{', '.join(regs)}}}, [r_ma{off}];")
+            for q in range(4):
+                self.e(f"add.rn.f32 {regs[q]}, {regs[q]}, {src(4 * h + q)};")
+            self.e(f"st.shared.v4.f32 [r_ma{off}], {{{', '.join(regs)}}};")
+
+
+class Fwd(Base):
+    """forward interpreter that also records the tape"""
+
+    def case(self, op, body):
+        self.e(f"FC{op}:")
+        body()
+        self.e("bra.uni FLOOP;")
+
+    def build(self):
+        K = self.K
+        A, L, T, c = self.vec("A"), self.vec("L"), self.vec("T"), (lambda j: "cv")
+        S = lambda d: (lambda j: f"S{d}_{j}")
+        regs = [f"{p}{j}" for p in "ALTVWM" for j in range(K)]
+        self.e("{")
+        self.e(".reg .f32 " + ", ".join(regs) + ", cv;")
+        self.e(".reg .f32 " + ", ".join(f"S{d}_{j}" for d in range(R) for j in range(K)) + ";")
+        self.e(".reg .pred " + ", ".join(f"P{j}" for j in range(K)) + ";")
+        self.e(".reg .u32 r_ptr, r_ix, r_iy, r_nx, r_ny, r_op, r_ad, r_xc, r_xstr, r_mo, r_moo, r_ma, r_flag, r_tape;")
+        self.e("mov.u32 r_ptr, %{pg};")
+        self.e("mov.u32 r_xc, %{xc};")
+        self.e("mov.u32 r_xstr, %{xstr};")
+        self.e("mov.u32 r_mo, %{mo};")
+        self.e("mov.u32 r_tape, %{tape};")
+        self.e("ld.shared.v2.u32 {r_nx, r_ny}, [r_ptr];")
+        self.e("FLOOP:")
+        self.e("mov.b32 r_ix, r_nx;")
+        self.e("mov.b32 r_iy, r_ny;")
+        self.e("ld.shared.v2.u32 {r_nx, r_ny}, [r_ptr+8];")
+        self.e("add.u32 r_ptr, r_ptr, 8;")
+        self.e("mov.b32 cv, r_iy;")
+        self.e("and.b32 r_op, r_ix, 255;")
+        self.e("FTS: .branchtargets " + ", ".join(f"FC{k}" for k in range(OP_COUNT)) + ";")
+        self.e("brx.idx.uni r_op, FTS;")
+        self.e(f"FC{OP_END_ROOT}:")
+        self.e("mov.u32 r_flag, 0;")
+        self.e("bra.uni FDONE;")
+        self.e(f"FC{OP_END_MODI}:")
+        self.e("mov.u32 r_flag, 1;")
+        self.e("bra.uni FDONE;")
+        self.case(OP_LDV, lambda: self.load_x(A))
+        self.case(OP_LDC, lambda: [self.e(f"mov.f32 A{j}, cv;") for j in range(K)])
+        for f in UNA:
+            def un(f=f):
+                self.fn1d(f, A, A, T)
+                self.tape_put(T)
+
+            def unv(f=f):
+                self.load_x(L)
+                self.fn1d(f, A, L, T)
+                self.tape_put(T)
+
+            def unm(f=f):
+                if not self.modi:
+                    return
+                self.fn1d(f, L, A, T)        # value into L (scratch), derivative into T
+                self.tape_put(T)
+                self.modi_add(L)
+
+            self.case(OP_UN + f - F_SIN, un)
+            self.case(OP_UNV + f - F_SIN, unv)
+            self.case(OP_UN_M + f - F_SIN, unm)
+        for f in BIN:
+            need = f in NEEDS_OPERAND
+
+            def bv(f=f, need=need, modi=False):
+                self.load_x(L)
+                if need:
+                    self.tape_put(A)
+                if modi:
+                    self.fn2(f, T, A, L)
+                    self.modi_add(T)
+                    for j in range(K):
+                        self.e(f"mov.f32 A{j}, L{j};")
+                else:
+                    self.fn2(f, A, A, L)
+
+            def bc(f=f, need=need, modi=False):
+                if need:
+                    self.tape_put(A)
+                if modi:
+                    self.fn2(f, T, A, c)
+                    self.modi_add(T)
+                    for j in range(K):
+                        self.e(f"mov.f32 A{j}, cv;")
+                else:
+                    self.fn2(f, A, A, c)
+
+            def rv(f=f, need=need, modi=False):
+                self.load_x(L)
+                if need:
+                    self.tape_put(A)
+                if modi:
+                    self.fn2(f, T, L, A)
+                    self.modi_add(T)
+                else:
+                    self.fn2(f, A, L, A)
+
+            def rc(f=f, need=need, modi=False):
+                if need:
+                    self.tape_put(A)
+                if modi:
+                    self.fn2(f, T, c, A)
+                    self.modi_add(T)
+                else:
+                    self.fn2(f, A, c, A)
+
+            self.case(OP_BV + f, bv)
+            self.case(OP_BC + f, bc)
+            self.case(OP_RV + f, rv)
+            self.case(OP_RC + f, rc)
+            for op, fn in ((OP_BV_M, bv), (OP_BC_M, bc), (OP_RV_M, rv), (OP_RC_M, rc)):
+                self.case(op + f, (lambda fn=fn: fn(modi=True)) if self.modi else (lambda: None))
+        for d in range(R):
+            def spv(d=d):
+                for j in range(K):
+                    self.e(f"mov.f32 S{d}_{j}, A{j};")
+                self.load_x(A)
+
+            def spc(d=d):
+                for j in range(K):
+                    self.e(f"mov.f32 S{d}_{j}, A{j};")
+                    self.e(f"mov.f32 A{j}, cv;")
+
+            self.case(OP_SPV + d, spv)
+            self.case(OP_SPC + d, spc)
+        for f in BIN:
+            need = f in NEEDS_OPERAND
+            for d in range(R):
+                def bs(f=f, d=d, need=need, modi=False):
+                    if need:
+                        self.tape_put(S(d))
+                        self.tape_put(A)
+                    if modi:
+                        self.fn2(f, T, S(d), A)
+                        self.modi_add(T)
+                    else:
+                        self.fn2(f, A, S(d), A)
+
+                def rs(f=f, d=d, need=need, modi=False):
+                    if need:
+                        self.tape_put(S(d))
+                        self.tape_put(A)
+                    if modi:
+                        self.fn2(f, T, A, S(d))
+                        self.modi_add(T)
+                        for j in range(K):
+                            self.e(f"mov.f32 A{j}, S{d}_{j};")
+                    else:
+                        self.fn2(f, A, A, S(d))
+
+                self.case(OP_BS + f * R + d, bs)
+                self.case(OP_RS + f * R + d, rs)
+                self.case(OP_BS_M + f * R + d, (lambda bs=bs: bs(modi=True)) if self.modi else (lambda: None))
+                self.case(OP_RS_M + f * R + d, (lambda rs=rs: rs(modi=True)) if self.modi else (lambda: None))
+        self.e("FDONE:")
+        for j in range(K):
+            self.e(f"mov.f32 %{{a{j}}}, A{j};")
+        self.e("mov.u32 %{flag}, r_flag;")
+        self.e("mov.u32 %{tend}, r_tape;")
+        self.e("}")
+        return "\n".join(self.lines)
+
+
+class Rev(Base):
+    """reverse sweep"""
+
+    def case(self, op, body):
+        self.e(f"RC{op}:")
+        body()
+        self.e("bra.uni RLOOP;")
+
+    # ---- accumulation targets
+    def gx_add(self, vals):
+        """gradient tile of X at the lane's points of feature r_iy += vals"""
+        self.e("mad.lo.u32 r_ad, r_iy, r_xstr, r_gx;")
+        for j in range(self.K):
+            off = 4 * j if j < 4 else 512 + 4 * (j - 4)
+            self.e(f"red.shared.add.f32 [r_ad+{off}], {vals(j)};")
+
+    def gc_add(self, vals):
+        """per-warp constant gradient [node] += sum over the warp's points"""
+        K = self.K
+        self.e(f"add.f32 q_s, {vals(0)}, {vals(1)};")
+        for j in range(2, K):
+            self.e(f"add.f32 q_s, q_s, {vals(j)};")
+        for m in (16, 8, 4, 2, 1):
+            self.e(f"shfl.sync.bfly.b32 q_t, q_s, {m}, 31, -1;")
+            self.e("add.f32 q_s, q_s, q_t;")
+        self.e("shr.u32 r_nd, r_ix, 16;")
+        self.e("mad.lo.u32 r_ca, r_nd, 4, r_cg;")
+        self.e("@PL ld.shared.f32 q_t, [r_ca];")
+        self.e("@PL add.f32 q_t, q_t, q_s;")
+        self.e("@PL st.shared.f32 [r_ca], q_t;")
+
+    def seed(self, dst):
+        """dst = seed of the output of this Modi instruction at the lane's points"""
+        self.e("bfe.u32 r_moo, r_ix, 8, 8;")
+        self.e(f"mad.lo.u32 r_ma, r_moo, {128 * self.K}, r_sd;")
+        for h in range(self.K // 4):
+            regs = ", ".join(dst(4 * h + q) for q in range(4))
+            off = f"+{512 * h}" if h else ""
+            self.e(f"ld.shared.v4.f32 {{{regs}}}, [r_ma{off}];")
+
+    def dfn2(self, f, a, b, g, da, db):
+        """da[j] = g*df/da, db[j] = g*df/db at (a[j], b[j]); None skips one"""
+        for j in range(self.K):
+            x, y, gg = a(j), b(j), g(j)
+            if f == F_ADD:
+                if da: self.e(f"mov.f32 {da(j)}, {gg};")
+                if db: self.e(f"mov.f32 {db(j)}, {gg};")
+            elif f == F_SUB:
+                if da: self.e(f"mov.f32 {da(j)}, {gg};")
+                if db: self.e(f"neg.f32 {db(j)}, {gg};")
+            elif f == F_MUL:
+                if da: self.e(f"mul.rn.f32 {da(j)}, {gg}, {y};")
+                if db: self.e(f"mul.rn.f32 {db(j)}, {gg}, {x};")
+            elif f == F_PDIV:
+                self.e(f"abs.f32 V{j}, {y};")
+                self.e(f"setp.gt.f32 P{j}, V{j}, {GUARD};")
+                self.e(f"rcp.approx.ftz.f32 V{j}, {y};")
+                self.e(f"mul.rn.f32 W{j}, {gg}, V{j};")          # g / b
+                if db:
+                    self.e(f"mul.rn.f32 V{j}, {x}, V{j};")       # a / b
+                    self.e(f"mul.rn.f32 V{j}, W{j}, V{j};")
+                    self.e(f"neg.f32 V{j}, V{j};")
+                    self.e(f"selp.f32 {db(j)}, V{j}, {ZERO}, P{j};")
+                if da:
+                    self.e(f"selp.f32 {da(j)}, W{j}, {ZERO}, P{j};")
+            elif f == F_MAX:
+                self.e(f"setp.ge.f32 P{j}, {x}, {y};")
+                self.e(f"setp.nan.f32 Q{j}, {y}, {y};")
+                self.e(f"or.pred P{j}, P{j}, Q{j};")
+                if da: self.e(f"selp.f32 {da(j)}, {gg}, {ZERO}, P{j};")
+                if db: self.e(f"selp.f32 {db(j)}, {ZERO}, {gg}, P{j};")
+
+    def addv(self, out, x, y):
+        for j in range(self.K):
+            self.e(f"add.f32 {out(j)}, {x(j)}, {y(j)};")
+
+    def build(self):
+        K = self.K
+        G, L, T1, T2 = self.vec("G"), self.vec("L"), self.vec("T"), self.vec("U")
+        DA, DB, SD = self.vec("DA"), self.vec("DB"), self.vec("SD")
+        GS = lambda d: (lambda j: f"GS{d}_{j}")
+        c = lambda j: "cv"
+        regs = [f"{p}{j}" for p in ("G", "L", "T", "U", "V", "W", "DA", "DB", "SD") for j in range(K)]
+        self.e("{")
+        self.e(".reg .f32 " + ", ".join(regs) + ", cv, q_s, q_t;")
+        self.e(".reg .f32 " + ", ".join(f"GS{d}_{j}" for d in range(R) for j in range(K)) + ";")
+        self.e(".reg .pred " + ", ".join([f"P{j}" for j in range(K)] + [f"Q{j}" for j in range(K)]) + ", PL;")
+        self.e(".reg .u32 r_ptr, r_ix, r_iy, r_nx, r_ny, r_op, r_ad, r_xc, r_xstr, r_gx, r_cg, r_sd, r_moo, r_ma, r_tape, r_nd, r_ca, r_lane, r_beg;")
+        self.e("mov.u32 r_ptr, %{plast};")
+        self.e("mov.u32 r_beg, %{pg};")
+        self.e("mov.u32 r_xc, %{xc};")
+        self.e("mov.u32 r_xstr, %{xstr};")
+        self.e("mov.u32 r_gx, %{gx};")
+        self.e("mov.u32 r_cg, %{cg};")
+        self.e("mov.u32 r_sd, %{sd};")
+        self.e("mov.u32 r_tape, %{tend};")
+        self.e("mov.u32 r_lane, %{lane};")
+        self.e("setp.eq.u32 PL, r_lane, 0;")
+        for j in range(K):
+            self.e(f"mov.f32 G{j}, %{{s{j}}};")
+        self.e("ld.shared.v2.u32 {r_nx, r_ny}, [r_ptr];")
+        self.e("RLOOP:")
+        self.e("mov.b32 r_ix, r_nx;")
+        self.e("mov.b32 r_iy, r_ny;")
+        # prefetch the previous instruction (one below the program start reads
+        # the word before it; that word is never used)
+        self.e("ld.shared.v2.u32 {r_nx, r_ny}, [r_ptr+-8];")
+        self.e("sub.u32 r_ptr, r_ptr, 8;")
+        self.e("mov.b32 cv, r_iy;")
+        self.e("and.b32 r_op, r_ix, 255;")
+        self.e("RTR: .branchtargets " + ", ".join(f"RC{k}" for k in range(OP_COUNT)) + ";")
+        self.e("brx.idx.uni r_op, RTR;")
+
+        # the program's terminator starts the sweep: the root's adjoint (END_ROOT)
+        # is the seed already in G; Modi trees start from zero
+        self.case(OP_END_ROOT, lambda: None)
+        self.case(OP_END_MODI, lambda: [self.e(f"mov.f32 G{j}, {ZERO};") for j in range(K)])
+
+        def done_if_first():
+            # the first instruction of a program loads a leaf into acc; its
+            # reverse ends the sweep
+            self.e("bra.uni RDONE;")
+
+        def ldv():
+            self.gx_add(G)
+
+        def ldc():
+            self.gc_add(G)
+
+        self.e(f"RC{OP_LDV}:")
+        ldv()
+        done_if_first()
+        self.e(f"RC{OP_LDC}:")
+        ldc()
+        done_if_first()
+        for f in UNA:
+            def un(f=f):
+                self.tape_get(T1)
+                for j in range(K):
+                    self.e(f"mul.rn.f32 G{j}, G{j}, T{j};")
+
+            def unv(f=f):
+                self.tape_get(T1)
+                for j in range(K):
+                    self.e(f"mul.rn.f32 DA{j}, G{j}, T{j};")
+                self.gx_add(DA)
+
+            def unm(f=f):
+                if not self.modi:
+                    return
+                self.tape_get(T1)
+                self.seed(SD)
+                for j in range(K):
+                    self.e(f"fma.rn.f32 G{j}, SD{j}, T{j}, G{j};")
+
+            self.case(OP_UN + f - F_SIN, un)
+            self.e(f"RC{OP_UNV + f - F_SIN}:")
+            unv()
+            done_if_first()
+            self.case(OP_UN_M + f - F_SIN, unm)
+
+        for f in BIN:
+            need = f in NEEDS_OPERAND
+
+            # BV: acc = f(a = acc_before, b = x)
+            def bv(f=f, need=need):
+                self.load_x(L)
+                if need:
+                    self.tape_get(T1)
+                self.dfn2(f, T1, L, G, DA, DB)
+                self.gx_add(DB)
+                for j in range(K):
+                    self.e(f"mov.f32 G{j}, DA{j};")
+
+            def bc(f=f, need=need):
+                if need:
+                    self.tape_get(T1)
+                self.dfn2(f, T1, c, G, DA, DB)
+                self.gc_add(DB)
+                for j in range(K):
+                    self.e(f"mov.f32 G{j}, DA{j};")
+
+            # RV: acc = f(a = x, b = acc_before)
+            def rv(f=f, need=need):
+                self.load_x(L)
+                if need:
+                    self.tape_get(T1)
+                self.dfn2(f, L, T1, G, DA, DB)
+                self.gx_add(DA)
+                for j in range(K):
+                    self.e(f"mov.f32 G{j}, DB{j};")
+
+            def rc(f=f, need=need):
+                if need:
+                    self.tape_get(T1)
+                self.dfn2(f, c, T1, G, DA, DB)
+                self.gc_add(DA)
+                for j in range(K):
+                    self.e(f"mov.f32 G{j}, DB{j};")
+
+            # Modi forms: the function value's adjoint is the output's seed
+            def bvm(f=f, need=need):      # out += f(acc, x); acc = x
+                self.load_x(L)
+                if need:
+                    self.tape_get(T1)
+                self.seed(SD)
+                self.dfn2(f, T1, L, SD, DA, DB)
+                self.addv(DB, DB, G)
+                self.gx_add(DB)
+                for j in range(K):
+                    self.e(f"mov.f32 G{j}, DA{j};")
+
+            def bcm(f=f, need=need):      # out += f(acc, c); acc = c
+                if need:
+                    self.tape_get(T1)
+                self.seed(SD)
+                self.dfn2(f, T1, c, SD, DA, DB)
+                self.addv(DB, DB, G)
+                self.gc_add(DB)
+                for j in range(K):
+                    self.e(f"mov.f32 G{j}, DA{j};")
+
+            def rvm(f=f, need=need):      # out += f(x, acc); acc unchanged
+                self.load_x(L)
+                if need:
+                    self.tape_get(T1)
+                self.seed(SD)
+                self.dfn2(f, L, T1, SD, DA, DB)
+                self.gx_add(DA)
+                self.addv(G, G, DB)
+
+            def rcm(f=f, need=need):      # out += f(c, acc); acc unchanged
+                if need:
+                    self.tape_get(T1)
+                self.seed(SD)
+                self.dfn2(f, c, T1, SD, DA, DB)
+                self.gc_add(DA)
+                self.addv(G, G, DB)
+
+            self.case(OP_BV + f, bv)
+            self.case(OP_BC + f, bc)
+            self.case(OP_RV + f, rv)
+            self.case(OP_RC + f, rc)
+            for op, fn in ((OP_BV_M, bvm), (OP_BC_M, bcm), (OP_RV_M, rvm), (OP_RC_M, rcm)):
+                self.case(op + f, fn if self.modi else (lambda: None))
+
+        for d in range(R):
+            def spv(d=d):
+                self.gx_add(G)
+                for j in range(K):
+                    self.e(f"mov.f32 G{j}, GS{d}_{j};")
+
+            def spc(d=d):
+                self.gc_add(G)
+                for j in range(K):
+                    self.e(f"mov.f32 G{j}, GS{d}_{j};")
+
+            self.case(OP_SPV + d, spv)
+            self.case(OP_SPC + d, spc)
+
+        for f in BIN:
+            need = f in NEEDS_OPERAND
+            for d in range(R):
+                # BS: acc = f(a = s[d], b = acc_before); tape: s[d] then acc
+                def bs(f=f, d=d, need=need):
+                    if need:
+                        self.tape_get(T2)        # acc_before (b)
+                        self.tape_get(T1)        # s[d] (a)
+                    self.dfn2(f, T1, T2, G, GS(d), DB)
+                    for j in range(K):
+                        self.e(f"mov.f32 G{j}, DB{j};")
+
+                # RS: acc = f(a = acc_before, b = s[d])
+                def rs(f=f, d=d, need=need):
+                    if need:
+                        self.tape_get(T2)        # acc_before (a)
+                        self.tape_get(T1)        # s[d] (b)
+                    self.dfn2(f, T2, T1, G, DA, GS(d))
+                    for j in range(K):
+                        self.e(f"mov.f32 G{j}, DA{j};")
+
+                def bsm(f=f, d=d, need=need):   # out += f(s[d], acc); acc unchanged
+                    if need:
+                        self.tape_get(T2)
+                        self.tape_get(T1)
+                    self.seed(SD)
+                    self.dfn2(f, T1, T2, SD, GS(d), DB)
+                    self.addv(G, G, DB)
+
+                def rsm(f=f, d=d, need=need):   # out += f(acc, s[d]); acc = s[d]
+                    if need:
+                        self.tape_get(T2)
+                        self.tape_get(T1)
+                    self.seed(SD)
+                    self.dfn2(f, T2, T1, SD, DA, DB)
+                    self.addv(GS(d), DB, G)
+                    for j in range(K):
+                        self.e(f"mov.f32 G{j}, DA{j};")
+
+                self.case(OP_BS + f * R + d, bs)
+                self.case(OP_RS + f * R + d, rs)
+                self.case(OP_BS_M + f * R + d, bsm if self.modi else (lambda: None))
+                self.case(OP_RS_M + f * R + d, rsm if self.modi else (lambda: None))
+        self.e("RDONE:")
+        self.e("}")
+        return "\n".join(self.lines)
+
+
+def _literal(body: str) -> str:
+    return "\n".join('      "' + l.replace("\\", "\\\\").replace('"', '\\"') + '\\n"'
+                     for l in body.split("\n"))
+
+
+def render_fwd(K, modi):
+    body = Fwd(K, modi).build()
+    names = [f"a{j}" for j in range(K)] + ["flag", "tend", "pg", "xc", "xstr", "mo", "tape"]
+    for i, n in enumerate(names):
+        body = body.replace("%{" + n + "}", f"%{i}")
+    outs = ", ".join([f'"=f"(acc[{j}])' for j in range(K)] + ['"=r"(flag)', '"=r"(tend)'])
+    return f"""template <>
+__device__ __forceinline__ unsigned bwd_forward<{K}, {'true' if modi else 'false'}>(
+    unsigned pg, unsigned xc, unsigned xstr, unsigned mo, unsigned tape, float (&acc)[{K}],
+    unsigned& tend) {{
+  unsigned flag;
+  asm volatile(
+{_literal(body)}
+      : {outs}
+      : "r"(pg), "r"(xc), "r"(xstr), "r"(mo), "r"(tape)
+      : "memory");
+  return flag;
+}}
+"""
+
+
+def render_rev(K, modi):
+    body = Rev(K, modi).build()
+    names = ["plast", "pg", "xc", "xstr", "gx", "cg", "sd", "tend", "lane"] + [f"s{j}" for j in range(K)]
+    for i, n in enumerate(names):
+        body = body.replace("%{" + n + "}", f"%{i}")
+    ins = ", ".join(['"r"(plast)', '"r"(pg)', '"r"(xc)', '"r"(xstr)', '"r"(gx)', '"r"(cg)', '"r"(sd)',
+                     '"r"(tend)', '"r"(lane)'] + [f'"f"(seed[{j}])' for j in range(K)])
+    return f"""template <>
+__device__ __forceinline__ void bwd_reverse<{K}, {'true' if modi else 'false'}>(
+    unsigned plast, unsigned pg, unsigned xc, unsigned xstr, unsigned gx, unsigned cg, unsigned sd,
+    unsigned tend, unsigned lane, const float (&seed)[{K}]) {{
+  asm volatile(
+{_literal(body)}
+      :
+      : {ins}
+      : "memory");
+}}
+"""
+
+
+def main():
+    parts = [
+        "// interp_bwd.cuh -- GENERATED by gen_interp_bwd.py; do not edit by hand.",
+        "// Forward-with-tape and reverse sweeps of the adjoint kernel (adjoint.cu).",
+        "#pragma once",
+        "namespace tgp {",
+        "template <int K, bool MODI>",
+        "__device__ __forceinline__ unsigned bwd_forward(unsigned pg, unsigned xc, unsigned xstr,",
+        "                                                unsigned mo, unsigned tape, float (&acc)[K],",
+        "                                                unsigned& tend);",
+        "template <int K, bool MODI>",
+        "__device__ __forceinline__ void bwd_reverse(unsigned plast, unsigned pg, unsigned xc,",
+        "                                            unsigned xstr, unsigned gx, unsigned cg,",
+        "                                            unsigned sd, unsigned tend, unsigned lane,",
+        "                                            const float (&seed)[K]);",
+    ]
+    for K, modi in ((4, False), (4, True)):
+        parts.append(render_fwd(K, modi))
+        parts.append(render_rev(K, modi))
+    parts.append("}  // namespace tgp")
+    open(OUT, "w").write("\n".join(parts) + "\n")
+    return OUT
+
+
+if __name__ == "__main__":
+    import sys
+    sys.path.insert(0, HERE)
+    print(main())

@@ -41,9 +41,11 @@ constexpr int MAX_OUT = 16;     // outputs
 constexpr int MAX_FEAT = 256;   // features
 
 // ------------------------------------------------------------- instruction set
-// One instruction is a uint2: .x = opcode | out_index << 8; .y = the leaf
-// operand (feature index for *V forms, float bits of the constant for *C
-// forms, slot-free forms ignore it).  f = function id 0..9, d = slot 0..7.
+// One instruction is a uint2: .x = opcode | out_index << 8 | leaf_node << 16;
+// .y = the leaf operand (feature index for *V forms, float bits of the
+// constant for *C forms).  leaf_node is the prefix position of the leaf
+// operand (used by the adjoint to route constant gradients).  f = function
+// id 0..9, d = slot 0..7.
 enum Op : uint32_t {
   OP_END_ROOT = 0,   // output 0 := acc (single output, no Modi node)
   OP_END_MODI = 1,   // outputs are the Modi accumulators
@@ -83,6 +85,8 @@ struct WsLayout {
   size_t plen;      // int32 [pop]        instruction count (0 = invalid tree)
   size_t status;    // int32 [pop]        per-tree status
   size_t partial;   // double [pop, n_out, n_groups]  per-item partial SSE
+  size_t gval64;    // double [pop, max_len]  constant gradients (adjoint)
+  size_t mse64;     // double [pop, n_out]    squared-residual sums (adjoint)
   size_t ctrl;      // uint32 [64]: [0] work counter, [1] any-Modi flag, [2] error word
   size_t total;
   int pcap;         // instructions per program slot (even)
@@ -141,6 +145,39 @@ struct FinalArgs {
   double* mse;
   long long pop;
   int O, n_groups;
+  long long D;
+};
+
+struct AdjArgs {
+  const uint2* prog;
+  const int* plen;
+  const int* status;
+  int pcap;
+  long long pop;
+  int max_len;
+  const float* X;
+  long long D;
+  int F;
+  long long ldx;
+  const float* y;      // [D, O]
+  int O;
+  const double* g;     // [pop, O] upstream gradient of the MSE
+  bool want_mse;       // accumulate the MSE too (else trees with g == 0 are skipped)
+  double* gval64;      // [pop, max_len] constant gradients (FP64)
+  double* mse64;       // [pop, O] sum of squared residuals (FP64)
+  float* grad_X;       // [D, F] accumulated into (may be null)
+  int tp, n_tiles;
+  unsigned* ctrl;
+};
+
+struct AdjFinalArgs {
+  const double* gval64;
+  const double* mse64;
+  const int* status;
+  float* grad_value;   // [pop, ld] or null
+  double* mse;         // [pop, O] or null
+  long long pop, ld;
+  int max_len, O;
   long long D;
 };
 
