@@ -145,6 +145,34 @@ tgp_status tgp_fitness_mse_cfg(const tgp_population* pop, const tgp_data* data, 
                                int32_t n_outputs, double* mse, int32_t* tree_status, void* ws,
                                size_t ws_bytes, void* stream, const tgp_config* cfg);
 
+/* One SR problem of a batch: its population, data, targets and outputs. */
+typedef struct tgp_problem {
+  tgp_population pop;
+  tgp_data data;
+  const float* y;         /* [device] [n_points, n_outputs]                  */
+  int32_t n_outputs;
+  double* mse;            /* [device] [pop, n_outputs] output                */
+  int32_t* tree_status;   /* [device] [pop] output, or NULL                  */
+  tgp_config cfg;         /* launch shape (all zero = heuristic); the events
+                             are ignored                                     */
+} tgp_problem;
+
+#define TGP_MAX_PROBLEMS 16
+
+/* Workspace bytes of tgp_batch_fitness_mse for these problems (0 = invalid). */
+size_t tgp_batch_workspace_size(const tgp_problem* probs, int32_t n);
+
+/* SR fitness of n independent problems of uneven sizes (populations, tree
+ * lengths, point counts, feature counts) in one stage launch, one persistent
+ * evaluation launch and one finalize launch (two evaluation launches when
+ * single-output and Modi populations are mixed).  The persistent CTAs pull
+ * work items of every problem from one counter, so small and large problems
+ * fill the GPU together.  Same per-problem results as tgp_fitness_mse.  All
+ * problems with one output must use the same points_per_lane.  Legal in
+ * stream capture (the batched call of one generation is a CUDA graph). */
+tgp_status tgp_batch_fitness_mse(const tgp_problem* probs, int32_t n, void* ws, size_t ws_bytes,
+                                 void* stream);
+
 /* Reverse-mode gradient of L = sum_{p,k} grad_mse[p,k] * MSE[p,k] (the
  * adjoint is not in the paper; it differentiates the Sec. III-C fitness).
  *   grad_mse   [device] double [pop, n_outputs]  upstream gradient

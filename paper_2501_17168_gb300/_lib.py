@@ -38,6 +38,14 @@ class tgp_config(ctypes.Structure):
                 ("eval_begin_event", ctypes.c_void_p), ("eval_end_event", ctypes.c_void_p)]
 
 
+class tgp_problem(ctypes.Structure):
+    _fields_ = [("pop", tgp_population), ("data", tgp_data), ("y", ctypes.c_void_p),
+                ("n_outputs", ctypes.c_int32), ("mse", ctypes.c_void_p),
+                ("tree_status", ctypes.c_void_p), ("cfg", tgp_config)]
+
+
+MAX_PROBLEMS = 16
+
 _P = ctypes.POINTER
 _lock = threading.Lock()
 _lib = None
@@ -62,6 +70,9 @@ _SIGS = {
                                            ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
                                            _P(tgp_config)]),
+    "tgp_batch_workspace_size": (ctypes.c_size_t, [_P(tgp_problem), ctypes.c_int32]),
+    "tgp_batch_fitness_mse": (ctypes.c_int, [_P(tgp_problem), ctypes.c_int32, ctypes.c_void_p,
+                                             ctypes.c_size_t, ctypes.c_void_p]),
     "tgp_eval_backward": (ctypes.c_int, [_P(tgp_population), _P(tgp_data), ctypes.c_void_p,
                                          ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,

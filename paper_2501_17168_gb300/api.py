@@ -211,3 +211,50 @@ def tgp_eval_backward(type_, val, size, X, y, grad_mse, n_outputs: int = 1, max_
                                 g.data_ptr(), ptr(mse), ptr(gv), ptr(grad_X), tree_status.data_ptr(),
                                 ws.data_ptr(), ws.numel(), _stream_handle(dev)), "tgp_eval_backward")
     return mse, gv, grad_X, tree_status
+
+
+class BatchProblem:
+    """One problem of a batched fitness call (device tensors)."""
+
+    def __init__(self, type_, val, size, X, y, n_outputs=1, max_len=None, config=None):
+        self.tensors = (type_, val, size, X, y)
+        self.n_outputs = n_outputs
+        self.pop = make_population(type_, val, size, max_len)
+        self.data = make_data(X)
+        _f32(y, "y")
+        if not y.is_contiguous() or y.numel() != self.data.n_points * n_outputs:
+            raise ValueError("y must be a contiguous [n_points, n_outputs] float32 tensor")
+        dev = X.device
+        self.mse = torch.empty((self.pop.pop, n_outputs), dtype=torch.float64, device=dev)
+        self.status = torch.empty(self.pop.pop, dtype=torch.int32, device=dev)
+        cfg = make_config(config)
+        self.cfg = cfg if cfg is not None else tgp_config()
+
+    def c_struct(self):
+        return _lib.tgp_problem(self.pop, self.data, self.tensors[4].data_ptr(), self.n_outputs,
+                                self.mse.data_ptr(), self.status.data_ptr(), self.cfg)
+
+
+def tgp_batch_workspace_size(problems) -> int:
+    arr = (_lib.tgp_problem * len(problems))(*[p.c_struct() for p in problems])
+    n = _lib.load().tgp_batch_workspace_size(arr, len(problems))
+    if n == 0:
+        raise _lib.TGPError(_lib.TGP_ERR_INVALID_ARG, "tgp_batch_workspace_size")
+    return int(n)
+
+
+def tgp_batch_fitness_mse(problems, ws=None):
+    """MSE of every problem in one batched launch; fills problem.mse/status."""
+    lib = _lib.load()
+    arr = (_lib.tgp_problem * len(problems))(*[p.c_struct() for p in problems])
+    dev = problems[0].tensors[3].device
+    n = lib.tgp_batch_workspace_size(arr, len(problems))
+    if n == 0:
+        raise _lib.TGPError(_lib.TGP_ERR_INVALID_ARG, "tgp_batch_workspace_size")
+    if ws is None:
+        ws = workspace(n, dev)
+    elif ws.numel() < n:
+        raise ValueError("workspace too small")
+    check(lib.tgp_batch_fitness_mse(arr, len(problems), ws.data_ptr(), ws.numel(), _stream_handle(dev)),
+          "tgp_batch_fitness_mse")
+    return [p.mse for p in problems]

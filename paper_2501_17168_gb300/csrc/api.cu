@@ -156,84 +156,6 @@ bool data_ok(const tgp_data* d) {
   return true;
 }
 
-tgp_status launch_stage(const tgp_population* pop, int F, int O, const WsLayout& w, char* ws,
-                        int32_t* user_status, cudaStream_t st, const DevInfo& dv) {
-  if (pop->pop == 0) return TGP_OK;
-  StageArgs a;
-  a.type = pop->type;
-  a.val = pop->value;
-  a.size = pop->size;
-  a.pop = pop->pop;
-  a.ld = pop->ld;
-  a.max_len = pop->max_len;
-  a.n_features = F;
-  a.n_outputs = O;
-  a.prog = reinterpret_cast<uint2*>(ws + w.prog);
-  a.pcap = w.pcap;
-  a.plen = reinterpret_cast<int*>(ws + w.plen);
-  a.status = reinterpret_cast<int*>(ws + w.status);
-  a.user_status = user_status;
-  a.ctrl = reinterpret_cast<unsigned*>(ws + w.ctrl);
-  const void* fn = stage_kernel_ptr();
-  size_t smem = stage_smem_bytes();
-  if (!ensure_smem(fn, smem)) return TGP_ERR_CUDA;
-  const int warps_per_cta = stage_threads() / 32;
-  long long grid = cdiv(pop->pop, warps_per_cta);
-  if (grid > (long long)dv.sms * 16) grid = (long long)dv.sms * 16;
-  void* args[] = {&a};
-  if (cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(stage_threads()), args, smem, st) != cudaSuccess)
-    return TGP_ERR_CUDA;
-  return TGP_OK;
-}
-
-// Launches the evaluation kernels (both variants for single-output
-// populations; each exits unless it matches the stage pass's Modi flag).
-tgp_status launch_eval(const tgp_population* pop, const tgp_data* data, const float* y, int O,
-                       float* out, const WsLayout& w, char* ws, const Shape& sh_plain,
-                       const Shape& sh_modi, cudaStream_t st, const DevInfo& dv, bool mse) {
-  for (int variant = 0; variant < 2; ++variant) {
-    const bool modi = variant == 1;
-    if (!modi && O > 1) continue;
-    const Shape& sh = modi ? sh_modi : sh_plain;
-    const void* fn = find_eval_kernel(sh.K, sh.nw, modi, !mse);
-    if (!fn) return TGP_ERR_UNSUPPORTED;
-    size_t smem = eval_smem_bytes(sh.K, sh.nw, modi, mse, sh.bt, w.pcap, sh.tp, data->n_features, O);
-    if (!ensure_smem(fn, smem)) return TGP_ERR_CUDA;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, sh.nw * 32, smem) != cudaSuccess)
-      return TGP_ERR_CUDA;
-    if (per_sm < 1) return TGP_ERR_UNSUPPORTED;
-    long long grid = (long long)dv.sms * per_sm;
-    if (grid > sh.n_items) grid = sh.n_items;
-    EvalArgs a;
-    a.prog = reinterpret_cast<const uint2*>(ws + w.prog);
-    a.plen = reinterpret_cast<const int*>(ws + w.plen);
-    a.status = reinterpret_cast<const int*>(ws + w.status);
-    a.pcap = w.pcap;
-    a.pop = pop->pop;
-    a.X = data->X;
-    a.D = data->n_points;
-    a.F = data->n_features;
-    a.ldx = data->ldx;
-    a.y = y;
-    a.O = O;
-    a.out = out;
-    a.partial = reinterpret_cast<double*>(ws + w.partial);
-    a.bt = sh.bt;
-    a.tp = sh.tp;
-    a.g = sh.g;
-    a.n_tiles = sh.n_tiles;
-    a.n_groups = sh.n_groups;
-    a.n_blocks = sh.n_blocks;
-    a.n_items = sh.n_items;
-    a.ctrl = reinterpret_cast<unsigned*>(ws + w.ctrl);
-    void* args[] = {&a};
-    if (cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(sh.nw * 32), args, smem, st) != cudaSuccess)
-      return TGP_ERR_CUDA;
-  }
-  return TGP_OK;
-}
-
 // Shapes of both kernel variants share n_groups so one partial buffer serves.
 bool shapes_for(const tgp_population* pop, const tgp_data* data, int O, const tgp_config* cfg,
                 bool mse, const DevInfo& dv, Shape* plain, Shape* modi) {
@@ -248,55 +170,256 @@ bool shapes_for(const tgp_population* pop, const tgp_data* data, int O, const tg
   return true;
 }
 
+// One problem of a launch after planning.
+struct Planned {
+  const tgp_population* pop;
+  const tgp_data* data;
+  const float* y;
+  int O;
+  float* out;
+  double* mse_out;
+  int32_t* status_out;
+  Shape sp, sm;     // plain / Modi kernel shapes, n_groups equalised
+  WsLayout w;       // offsets relative to base
+  size_t base;      // offset of this problem's workspace region
+};
+
+tgp_status plan(Planned& q, const tgp_config* cfg, bool mse, const DevInfo& dv) {
+  if (!shapes_for(q.pop, q.data, q.O, cfg, mse, dv, &q.sp, &q.sm)) return TGP_ERR_UNSUPPORTED;
+  const int n_groups = q.sm.n_groups > q.sp.n_groups ? q.sm.n_groups : q.sp.n_groups;
+  q.w = ws_layout(q.pop->pop, q.pop->max_len, q.O, mse ? n_groups : 0);
+  for (Shape* sh : {&q.sp, &q.sm}) {
+    sh->n_groups = n_groups;
+    sh->g = (int)cdiv(sh->n_tiles, n_groups);
+    sh->n_items = (long long)sh->n_blocks * n_groups;
+  }
+  return TGP_OK;
+}
+
+tgp_status launch_stage(Planned* qs, int n, char* ws, cudaStream_t st, const DevInfo& dv) {
+  StageBatch b{};
+  long long total = 0;
+  int m = 0;
+  for (int i = 0; i < n; ++i) {
+    const Planned& q = qs[i];
+    if (q.pop->pop == 0) continue;
+    char* w = ws + q.base;
+    StageArgs& a = b.p[m];
+    a.type = q.pop->type;
+    a.val = q.pop->value;
+    a.size = q.pop->size;
+    a.pop = q.pop->pop;
+    a.ld = q.pop->ld;
+    a.max_len = q.pop->max_len;
+    a.n_features = q.data->n_features;
+    a.n_outputs = q.O;
+    a.prog = reinterpret_cast<uint2*>(w + q.w.prog);
+    a.pcap = q.w.pcap;
+    a.plen = reinterpret_cast<int*>(w + q.w.plen);
+    a.status = reinterpret_cast<int*>(w + q.w.status);
+    a.user_status = q.status_out;
+    a.ctrl = reinterpret_cast<unsigned*>(w + q.w.ctrl);
+    total += q.pop->pop;
+    b.end[m] = total;
+    ++m;
+  }
+  if (m == 0) return TGP_OK;
+  b.n = m;
+  const void* fn = stage_kernel_ptr();
+  size_t smem = stage_smem_bytes();
+  if (!ensure_smem(fn, smem)) return TGP_ERR_CUDA;
+  const int warps_per_cta = stage_threads() / 32;
+  long long grid = cdiv(total, warps_per_cta);
+  if (grid > (long long)dv.sms * 16) grid = (long long)dv.sms * 16;
+  void* args[] = {&b};
+  if (cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(stage_threads()), args, smem, st) != cudaSuccess)
+    return TGP_ERR_CUDA;
+  return TGP_OK;
+}
+
+// Launches the evaluation kernels over every problem's work items (the plain
+// variant only when some problem has a single output; each variant skips the
+// items of problems whose Modi flag does not match it).
+tgp_status launch_eval(Planned* qs, int n, char* ws, unsigned* counters, cudaStream_t st,
+                       const DevInfo& dv, bool mse) {
+  bool any_single = false;
+  for (int i = 0; i < n; ++i) any_single |= qs[i].O == 1;
+  for (int variant = 0; variant < 2; ++variant) {
+    const bool modi = variant == 1;
+    if (!modi && !any_single) continue;
+    EvalBatch b{};
+    b.counter = counters + (modi ? CTRL_COUNTER_MODI : CTRL_COUNTER);
+    long long total = 0;
+    size_t smem = 0;
+    int K = 0, nw = 0, m = 0;
+    for (int i = 0; i < n; ++i) {
+      const Planned& q = qs[i];
+      if (q.pop->pop == 0 || q.data->n_points == 0) continue;
+      if (!modi && q.O > 1) continue;
+      const Shape& sh = modi ? q.sm : q.sp;
+      if (m > 0 && (sh.K != K || sh.nw != nw)) return TGP_ERR_UNSUPPORTED;
+      K = sh.K;
+      nw = sh.nw;
+      char* w = ws + q.base;
+      EvalArgs& a = b.p[m];
+      a.prog = reinterpret_cast<const uint2*>(w + q.w.prog);
+      a.plen = reinterpret_cast<const int*>(w + q.w.plen);
+      a.status = reinterpret_cast<const int*>(w + q.w.status);
+      a.pcap = q.w.pcap;
+      a.pop = q.pop->pop;
+      a.X = q.data->X;
+      a.D = q.data->n_points;
+      a.F = q.data->n_features;
+      a.ldx = q.data->ldx;
+      a.y = q.y;
+      a.O = q.O;
+      a.out = q.out;
+      a.partial = reinterpret_cast<double*>(w + q.w.partial);
+      a.bt = sh.bt;
+      a.tp = sh.tp;
+      a.g = sh.g;
+      a.n_tiles = sh.n_tiles;
+      a.n_groups = sh.n_groups;
+      a.n_blocks = sh.n_blocks;
+      a.n_items = sh.n_items;
+      a.ctrl = reinterpret_cast<unsigned*>(w + q.w.ctrl);
+      total += sh.n_items;
+      b.end[m] = total;
+      size_t sb = eval_smem_bytes(sh.K, sh.nw, modi, mse, sh.bt, q.w.pcap, sh.tp, q.data->n_features, q.O);
+      if (sb > smem) smem = sb;
+      ++m;
+    }
+    if (m == 0) continue;
+    b.n = m;
+    const void* fn = find_eval_kernel(K, nw, modi, !mse);
+    if (!fn) return TGP_ERR_UNSUPPORTED;
+    if (smem > (size_t)dv.smem_optin) return TGP_ERR_UNSUPPORTED;
+    if (!ensure_smem(fn, smem)) return TGP_ERR_CUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nw * 32, smem) != cudaSuccess)
+      return TGP_ERR_CUDA;
+    if (per_sm < 1) return TGP_ERR_UNSUPPORTED;
+    long long grid = (long long)dv.sms * per_sm;
+    if (grid > total) grid = total;
+    void* args[] = {&b};
+    if (cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(nw * 32), args, smem, st) != cudaSuccess)
+      return TGP_ERR_CUDA;
+  }
+  return TGP_OK;
+}
+
+tgp_status launch_final(Planned* qs, int n, char* ws, cudaStream_t st) {
+  FinalBatch b{};
+  long long total = 0;
+  int m = 0;
+  for (int i = 0; i < n; ++i) {
+    const Planned& q = qs[i];
+    if (q.pop->pop == 0) continue;
+    char* w = ws + q.base;
+    FinalArgs& f = b.p[m];
+    f.partial = reinterpret_cast<const double*>(w + q.w.partial);
+    f.status = reinterpret_cast<const int*>(w + q.w.status);
+    f.mse = q.mse_out;
+    f.pop = q.pop->pop;
+    f.O = q.O;
+    f.n_groups = q.sp.n_groups;
+    f.D = q.data->n_points;
+    total += q.pop->pop * q.O;
+    b.end[m] = total;
+    ++m;
+  }
+  if (m == 0) return TGP_OK;
+  b.n = m;
+  void* args[] = {&b};
+  if (cudaLaunchKernel(finalize_kernel_ptr(), dim3((unsigned)cdiv(total, 256)), dim3(256), args, 0, st) !=
+      cudaSuccess)
+    return TGP_ERR_CUDA;
+  return TGP_OK;
+}
+
+bool problem_ok(const tgp_population* pop, const tgp_data* data, int O) {
+  return pop_ok(pop) && data_ok(data) && O >= 1 && O <= TGP_MAX_OUTPUTS;
+}
+
 tgp_status run(const tgp_population* pop, const tgp_data* data, const float* y, int O, float* out,
                double* mse_out, bool mse, int32_t* tree_status, void* ws, size_t ws_bytes,
                void* stream, const tgp_config* cfg) {
-  if (!pop_ok(pop) || !data_ok(data) || O < 1 || O > TGP_MAX_OUTPUTS) return TGP_ERR_INVALID_ARG;
+  if (!problem_ok(pop, data, O)) return TGP_ERR_INVALID_ARG;
   if (mse && (data->n_points < 1 || (pop->pop > 0 && (!y || !mse_out)))) return TGP_ERR_INVALID_ARG;
   if (!mse && pop->pop > 0 && data->n_points > 0 && !out) return TGP_ERR_INVALID_ARG;
   DevInfo dv;
   if (!dev_info(&dv)) return TGP_ERR_CUDA;
-  Shape sp, sm;
-  if (!shapes_for(pop, data, O, cfg, mse, dv, &sp, &sm)) return TGP_ERR_UNSUPPORTED;
-  const int n_groups = sm.n_groups > sp.n_groups ? sm.n_groups : sp.n_groups;
-  WsLayout w = ws_layout(pop->pop, pop->max_len, O, mse ? n_groups : 0);
-  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < w.total) return TGP_ERR_WORKSPACE;
+  Planned q{pop, data, y, O, out, mse_out, tree_status};
+  q.base = 0;
+  tgp_status s = plan(q, cfg, mse, dv);
+  if (s != TGP_OK) return s;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < q.w.total) return TGP_ERR_WORKSPACE;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* wsb = reinterpret_cast<char*>(ws);
-  if (cudaMemsetAsync(wsb + w.ctrl, 0, CTRL_WORDS * 4, st) != cudaSuccess) return TGP_ERR_CUDA;
-  tgp_status s = launch_stage(pop, data->n_features, O, w, wsb, tree_status, st, dv);
+  if (cudaMemsetAsync(wsb + q.w.ctrl, 0, CTRL_WORDS * 4, st) != cudaSuccess) return TGP_ERR_CUDA;
+  s = launch_stage(&q, 1, wsb, st, dv);
   if (s != TGP_OK) return s;
   if (pop->pop == 0 || data->n_points == 0) return TGP_OK;
-  // both variants must agree on n_groups for the shared partial layout
-  sp.n_groups = sm.n_groups = n_groups;
-  sp.g = (int)cdiv(sp.n_tiles, n_groups);
-  sm.g = (int)cdiv(sm.n_tiles, n_groups);
-  sp.n_items = (long long)sp.n_blocks * n_groups;
-  sm.n_items = (long long)sm.n_blocks * n_groups;
   if (cfg && cfg->eval_begin_event &&
       cudaEventRecord(reinterpret_cast<cudaEvent_t>(cfg->eval_begin_event), st) != cudaSuccess)
     return TGP_ERR_CUDA;
-  s = launch_eval(pop, data, y, O, out, w, wsb, sp, sm, st, dv, mse);
+  s = launch_eval(&q, 1, wsb, reinterpret_cast<unsigned*>(wsb + q.w.ctrl), st, dv, mse);
   if (s != TGP_OK) return s;
   if (cfg && cfg->eval_end_event &&
       cudaEventRecord(reinterpret_cast<cudaEvent_t>(cfg->eval_end_event), st) != cudaSuccess)
     return TGP_ERR_CUDA;
-  if (mse) {
-    FinalArgs f;
-    f.partial = reinterpret_cast<const double*>(wsb + w.partial);
-    f.status = reinterpret_cast<const int*>(wsb + w.status);
-    f.mse = mse_out;
-    f.pop = pop->pop;
-    f.O = O;
-    f.n_groups = n_groups;
-    f.D = data->n_points;
-    void* args[] = {&f};
-    long long n = pop->pop * O;
-    if (cudaLaunchKernel(finalize_kernel_ptr(), dim3((unsigned)cdiv(n, 256)), dim3(256), args, 0, st) !=
-        cudaSuccess)
-      return TGP_ERR_CUDA;
-  }
+  if (mse) return launch_final(&q, 1, wsb, st);
   return TGP_OK;
+}
+
+// Several independent problems in one stage, one persistent evaluation and one
+// finalize launch.  Workspace: a 256-byte control block (the shared work
+// counters) followed by one region per problem.
+tgp_status plan_batch(const tgp_problem* probs, int n, const DevInfo& dv, Planned* qs, size_t* total) {
+  if (n < 1 || n > TGP_MAX_PROBLEMS || !probs) return TGP_ERR_INVALID_ARG;
+  size_t off = al256(CTRL_WORDS * 4);
+  for (int i = 0; i < n; ++i) {
+    const tgp_problem& p = probs[i];
+    if (!problem_ok(&p.pop, &p.data, p.n_outputs)) return TGP_ERR_INVALID_ARG;
+    if (p.data.n_points < 1 || (p.pop.pop > 0 && (!p.y || !p.mse))) return TGP_ERR_INVALID_ARG;
+    Planned& q = qs[i];
+    q = Planned{&p.pop, &p.data, p.y, p.n_outputs, nullptr, p.mse, p.tree_status};
+    const tgp_config* cfg = (p.cfg.trees_per_block || p.cfg.points_per_tile || p.cfg.tiles_per_item ||
+                             p.cfg.points_per_lane)
+                                ? &p.cfg
+                                : nullptr;
+    tgp_status s = plan(q, cfg, true, dv);
+    if (s != TGP_OK) return s;
+    q.base = off;
+    off = al256(off + q.w.total);
+  }
+  // one launch needs one points-per-lane value per kernel variant
+  for (int i = 1; i < n; ++i) {
+    if (qs[i].O == 1 && qs[0].O == 1 && qs[i].sp.K != qs[0].sp.K) return TGP_ERR_UNSUPPORTED;
+  }
+  *total = off;
+  return TGP_OK;
+}
+
+tgp_status run_batch(const tgp_problem* probs, int n, void* ws, size_t ws_bytes, void* stream) {
+  DevInfo dv;
+  if (!dev_info(&dv)) return TGP_ERR_CUDA;
+  Planned qs[TGP_MAX_PROBLEMS];
+  size_t need = 0;
+  tgp_status s = plan_batch(probs, n, dv, qs, &need);
+  if (s != TGP_OK) return s;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < need) return TGP_ERR_WORKSPACE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* wsb = reinterpret_cast<char*>(ws);
+  if (cudaMemsetAsync(wsb, 0, CTRL_WORDS * 4, st) != cudaSuccess) return TGP_ERR_CUDA;
+  for (int i = 0; i < n; ++i)
+    if (cudaMemsetAsync(wsb + qs[i].base + qs[i].w.ctrl, 0, CTRL_WORDS * 4, st) != cudaSuccess)
+      return TGP_ERR_CUDA;
+  s = launch_stage(qs, n, wsb, st, dv);
+  if (s != TGP_OK) return s;
+  s = launch_eval(qs, n, wsb, reinterpret_cast<unsigned*>(wsb), st, dv, true);
+  if (s != TGP_OK) return s;
+  return launch_final(qs, n, wsb, st);
 }
 
 // Fused forward + reverse sweep: one CTA per point tile over all trees.
@@ -319,7 +442,10 @@ tgp_status run_backward(const tgp_population* pop, const tgp_data* data, const f
   if (pop->pop == 0) return TGP_OK;
   if (cudaMemsetAsync(wsb + w.gval64, 0, w.mse64 + (size_t)pop->pop * O * 8 - w.gval64, st) != cudaSuccess)
     return TGP_ERR_CUDA;
-  tgp_status s = launch_stage(pop, data->n_features, O, w, wsb, tree_status, st, dv);
+  Planned q{pop, data, y, O, nullptr, mse_out, tree_status};
+  q.w = w;
+  q.base = 0;
+  tgp_status s = launch_stage(&q, 1, wsb, st, dv);
   if (s != TGP_OK) return s;
   const int K = 4, nw = 8;
   for (int variant = 0; variant < 2; ++variant) {
@@ -422,7 +548,11 @@ tgp_status tgp_validate(const tgp_population* pop, int32_t n_features, int32_t n
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* wsb = reinterpret_cast<char*>(ws);
   if (cudaMemsetAsync(wsb + w.ctrl, 0, CTRL_WORDS * 4, st) != cudaSuccess) return TGP_ERR_CUDA;
-  return launch_stage(pop, n_features, n_outputs, w, wsb, tree_status, st, dv);
+  tgp_data dummy{nullptr, 0, n_features, n_features};
+  Planned q{pop, &dummy, nullptr, n_outputs, nullptr, nullptr, tree_status};
+  q.w = w;
+  q.base = 0;
+  return launch_stage(&q, 1, wsb, st, dv);
 }
 
 tgp_status tgp_eval_forward_cfg(const tgp_population* pop, const tgp_data* data, int32_t n_outputs,
@@ -457,6 +587,20 @@ tgp_status tgp_eval_backward(const tgp_population* pop, const tgp_data* data, co
                              size_t ws_bytes, void* stream) {
   return run_backward(pop, data, y, n_outputs, grad_mse, mse_out, grad_value, grad_X, tree_status, ws,
                       ws_bytes, stream);
+}
+
+size_t tgp_batch_workspace_size(const tgp_problem* probs, int32_t n) {
+  DevInfo dv;
+  if (!dev_info(&dv)) return 0;
+  Planned qs[TGP_MAX_PROBLEMS];
+  size_t need = 0;
+  if (plan_batch(probs, n, dv, qs, &need) != TGP_OK) return 0;
+  return need;
+}
+
+tgp_status tgp_batch_fitness_mse(const tgp_problem* probs, int32_t n, void* ws, size_t ws_bytes,
+                                 void* stream) {
+  return run_batch(probs, n, ws, ws_bytes, stream);
 }
 
 tgp_status tgp_check_device_error(void* ws, size_t ws_bytes, void* stream) {

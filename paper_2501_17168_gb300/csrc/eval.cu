@@ -126,33 +126,16 @@ __host__ __device__ inline EvalSmem eval_smem_layout(int K, int nw, bool modi, b
 
 // ----------------------------------------------------------- kernel
 template <int K, int NW, bool MODI, bool OUT>
-__global__ void __launch_bounds__(NW * 32, 2) eval_kernel(EvalArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__global__ void __launch_bounds__(NW * 32, 2) eval_kernel(const __grid_constant__ EvalBatch b) {
+  extern __shared__ __align__(16) unsigned char smem_all[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int CH = 32 * K;
-
-  // Which kernel serves a single-output population depends on whether the
-  // stage pass found a Modi node; the other variant leaves at once.
-  if (a.O == 1) {
-    const bool any_modi = *((volatile unsigned*)&a.ctrl[CTRL_ANY_MODI]) != 0;
-    if (any_modi != MODI) return;
-  }
-
-  const EvalSmem lay = eval_smem_layout(K, NW, MODI, !OUT, a.bt, a.pcap, a.tp, a.F, a.O);
-  uint2* prog_s = reinterpret_cast<uint2*>(smem + lay.prog);
-  float* xs = reinterpret_cast<float*>(smem + lay.xs);
-  float* ys = reinterpret_cast<float*>(smem + lay.ys);
-  float* mo = reinterpret_cast<float*>(smem + lay.mo) + warp * a.O * CH;
-  float* cpart = reinterpret_cast<float*>(smem + lay.cpart);
-  double* tacc = reinterpret_cast<double*>(smem + lay.tacc);
-  int* order = reinterpret_cast<int*>(smem + lay.order);
-  int* lens = reinterpret_cast<int*>(smem + lay.lens);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + lay.misc);
-  long long* s_item = reinterpret_cast<long long*>(smem + lay.misc + 8);
-  int* s_sub = reinterpret_cast<int*>(smem + lay.misc + 16);
-  const int XS = lay.xs_stride;
-  const int cpt = a.tp / CH;
-  const int O = a.O;
+  // fixed words first, the per-problem layout after them
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_all);
+  long long* s_item = reinterpret_cast<long long*>(smem_all + 8);
+  int* s_sub = reinterpret_cast<int*>(smem_all + 16);
+  unsigned char* smem = smem_all + 64;
+  const long long total = b.end[b.n - 1];
 
   if (tid == 0) {
     mbar_init(mbar, 1);
@@ -162,10 +145,34 @@ __global__ void __launch_bounds__(NW * 32, 2) eval_kernel(EvalArgs a) {
   uint32_t phase = 0;
 
   for (;;) {
-    if (tid == 0) *s_item = (long long)atomicAdd(&a.ctrl[CTRL_COUNTER], 1u);
+    if (tid == 0) *s_item = (long long)atomicAdd(b.counter, 1u);
     __syncthreads();
-    const long long item = *s_item;
-    if (item >= a.n_items) break;
+    const long long gitem = *s_item;
+    if (gitem >= total) break;
+    const int pi = batch_find(b.end, b.n, gitem);
+    const EvalArgs& a = b.p[pi];
+    const long long item = gitem - (pi ? b.end[pi - 1] : 0);
+    // Which kernel serves a single-output population depends on whether the
+    // stage pass found a Modi node; the other variant skips its items.
+    if (a.O == 1) {
+      const bool any_modi = *((volatile unsigned*)&a.ctrl[CTRL_ANY_MODI]) != 0;
+      if (any_modi != MODI) {
+        __syncthreads();
+        continue;
+      }
+    }
+    const EvalSmem lay = eval_smem_layout(K, NW, MODI, !OUT, a.bt, a.pcap, a.tp, a.F, a.O);
+    uint2* prog_s = reinterpret_cast<uint2*>(smem + lay.prog);
+    float* xs = reinterpret_cast<float*>(smem + lay.xs);
+    float* ys = reinterpret_cast<float*>(smem + lay.ys);
+    float* mo = reinterpret_cast<float*>(smem + lay.mo) + warp * a.O * CH;
+    float* cpart = reinterpret_cast<float*>(smem + lay.cpart);
+    double* tacc = reinterpret_cast<double*>(smem + lay.tacc);
+    int* order = reinterpret_cast<int*>(smem + lay.order);
+    int* lens = reinterpret_cast<int*>(smem + lay.lens);
+    const int XS = lay.xs_stride;
+    const int cpt = a.tp / CH;
+    const int O = a.O;
     const int grp = (int)(item / a.n_blocks);
     const long long blk = item - (long long)grp * a.n_blocks;
     const long long t0 = blk * a.bt;
@@ -323,9 +330,12 @@ __global__ void __launch_bounds__(NW * 32, 2) eval_kernel(EvalArgs a) {
 }
 
 // MSE[p,k] = (sum of the tile-group partials in order) / D; NaN for invalid trees.
-__global__ void finalize_kernel(FinalArgs a) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.pop * a.O) return;
+__global__ void finalize_kernel(const __grid_constant__ FinalBatch b) {
+  const long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= b.end[b.n - 1]) return;
+  const int pi = batch_find(b.end, b.n, gi);
+  const FinalArgs& a = b.p[pi];
+  const long long i = gi - (pi ? b.end[pi - 1] : 0);
   const long long p = i / a.O;
   double s = 0.0;
   const double* src = a.partial + i * a.n_groups;
@@ -355,7 +365,7 @@ const void* find_eval_kernel(int K, int nw, bool modi, bool out) {
 }
 
 size_t eval_smem_bytes(int K, int nw, bool modi, bool mse, int bt, int pcap, int tp, int F, int O) {
-  return eval_smem_layout(K, nw, modi, mse, bt, pcap, tp, F, O).total;
+  return 64 + eval_smem_layout(K, nw, modi, mse, bt, pcap, tp, F, O).total;
 }
 
 const void* finalize_kernel_ptr() { return (const void*)finalize_kernel; }

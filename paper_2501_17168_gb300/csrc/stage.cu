@@ -31,13 +31,17 @@ __device__ __forceinline__ bool is_int(float v) { return isfinite(v) && v == flo
 
 __device__ __forceinline__ int kind_of(uint32_t in) { return (in >> 4) & 3; }
 
-__global__ void __launch_bounds__(STAGE_WARPS * 32) stage_kernel(StageArgs a) {
+__global__ void __launch_bounds__(STAGE_WARPS * 32) stage_kernel(const __grid_constant__ StageBatch b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   NodeSmem& ns = reinterpret_cast<NodeSmem*>(smem_raw)[warp];
+  const long long total = b.end[b.n - 1];
 
-  for (long long p = (long long)blockIdx.x * STAGE_WARPS + warp; p < a.pop;
-       p += (long long)gridDim.x * STAGE_WARPS) {
+  for (long long gt = (long long)blockIdx.x * STAGE_WARPS + warp; gt < total;
+       gt += (long long)gridDim.x * STAGE_WARPS) {
+    const int pi = batch_find(b.end, b.n, gt);
+    const StageArgs& a = b.p[pi];
+    const long long p = gt - (pi ? b.end[pi - 1] : 0);
     const float* T = a.type + p * a.ld;
     const float* V = a.val + p * a.ld;
     const float* S = a.size + p * a.ld;

@@ -181,8 +181,38 @@ struct AdjFinalArgs {
   long long D;
 };
 
+// Several problems in one launch: a table of per-problem arguments passed as
+// a __grid_constant__ kernel parameter; global indices (work items, trees,
+// outputs) are split by the cumulative counts.
+constexpr int MAX_PROBLEMS = 16;
+
+struct StageBatch {
+  int n;
+  long long end[MAX_PROBLEMS];       // cumulative tree counts
+  StageArgs p[MAX_PROBLEMS];
+};
+
+struct EvalBatch {
+  int n;
+  unsigned* counter;                 // work counter of this kernel variant
+  long long end[MAX_PROBLEMS];       // cumulative work items
+  EvalArgs p[MAX_PROBLEMS];
+};
+
+struct FinalBatch {
+  int n;
+  long long end[MAX_PROBLEMS];       // cumulative pop * n_outputs
+  FinalArgs p[MAX_PROBLEMS];
+};
+
+__host__ __device__ inline int batch_find(const long long* end, int n, long long g) {
+  int i = 0;
+  while (i < n - 1 && g >= end[i]) ++i;
+  return i;
+}
+
 // control word indices
-enum { CTRL_COUNTER = 0, CTRL_ANY_MODI = 1, CTRL_ERROR = 2, CTRL_WORDS = 64 };
+enum { CTRL_COUNTER = 0, CTRL_ANY_MODI = 1, CTRL_ERROR = 2, CTRL_COUNTER_MODI = 3, CTRL_WORDS = 64 };
 // bits of the error word
 enum { ERR_MBAR_TIMEOUT = 1 };
 
