@@ -57,6 +57,8 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--pop", type=int, default=5000, help="trees (smaller cases for profiling)")
     ap.add_argument("--points", type=int, default=100_000, help="data points")
+    ap.add_argument("--suite", action="store_true",
+                    help="also time the other workloads (one JSON line each, after the main line)")
     return ap.parse_args()
 
 
@@ -370,6 +372,132 @@ def e2e(prob, dev, a, units):
             "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * T / a.steps}
 
 
+# ----------------------------------------------------------------- other workloads
+def _timed(fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _gpu_targets(api, prob, dev):
+    import torch
+    X = torch.from_numpy(prob.X).to(dev)
+    gt_t, gt_v, gt_s = api.population_to(prob.gt, dev)
+    gy, _ = api.tgp_eval_forward(gt_t, gt_v, gt_s, X, 1, max_len=prob.gt.max_len)
+    noise = torch.from_numpy(prob.noise).to(dev)
+    return X, (gy[:, 0, :].t() + noise).contiguous()
+
+
+def suite_lines(dev, steps):
+    """sr_small latency, batched uneven (one launch vs one launch per problem,
+    graph replay), differentiation and Modi forward + adjoint."""
+    import torch
+    from paper_2501_17168_gb300 import api, autograd as ag, workloads as W
+    hbm_gbs, sm_max_mhz, _ = _peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    f_hz = sm_max_mhz * 1e6
+    out = []
+
+    # sr_small: 64 trees x 256 points -- latency bound
+    prob = W.sr_small(0)
+    t, v, s = api.population_to(prob.pop, dev)
+    X, y = _gpu_targets(api, prob, dev)
+    ms = _timed(lambda: api.tgp_fitness_mse(t, v, s, X, y, 1, max_len=prob.pop.max_len), 200, 20)
+    out.append({"workload": "sr_small: 64 trees len<=63 x 256 points, forward + MSE",
+                "us_per_call": 1e3 * ms, "node_points_per_s": prob.pop.nodes() * prob.D / (ms / 1e3)})
+
+    # batched uneven: 8 problems in one persistent launch vs one launch per problem
+    probs = W.batched_uneven(0)
+    bps, units, t_sfu = [], 0.0, 0.0
+    for pr in probs:
+        tt, vv, ss = api.population_to(pr.pop, dev)
+        Xp, yp = _gpu_targets(api, pr, dev)
+        bps.append(api.BatchProblem(tt, vv, ss, Xp, yp, 1, max_len=pr.pop.max_len))
+        units += pr.pop.nodes() * pr.D
+        t_sfu += _roofline_time(pr.pop, pr.D, sms, f_hz, hbm_gbs)[1]
+    ms_batch = _timed(lambda: api.tgp_batch_fitness_mse(bps), steps, 2)
+
+    def per_problem():
+        for bp in bps:
+            tt, vv, ss, Xp, yp = bp.tensors
+            api.tgp_fitness_mse(tt, vv, ss, Xp, yp, 1, max_len=bp.pop.max_len, mse=bp.mse,
+                                tree_status=bp.status)
+    ms_each = _timed(per_problem, steps, 2)
+    n = api.tgp_batch_workspace_size(bps)
+    ws = torch.empty(n, dtype=torch.uint8, device=dev)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        api.tgp_batch_fitness_mse(bps, ws=ws)
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        api.tgp_batch_fitness_mse(bps, ws=ws)
+    ms_graph = _timed(graph.replay, steps, 2)
+    out.append({"workload": "batched_uneven: 8 problems, P 2,990-19,622, D 3,122-381,279, F 5-30, "
+                            "len U[7,511]; forward + MSE",
+                "node_points": units, "ms_batched": ms_batch, "ms_graph_replay": ms_graph,
+                "ms_one_launch_per_problem": ms_each,
+                "node_points_per_s_batched": units / (ms_batch / 1e3),
+                "node_points_per_s_graph": units / (ms_graph / 1e3),
+                "node_points_per_s_per_problem": units / (ms_each / 1e3),
+                "speedup_vs_per_problem": ms_each / ms_batch,
+                "roofline_frac_graph": (t_sfu * 1e3) / ms_graph})
+
+    # differentiation: forward MSE, fused forward + adjoint, one Adam step
+    for name, prob, O in (("diff: 10,000 trees len<=127 (<=16 constants) x 200,000 points, F=4",
+                           W.diff(0), 1),
+                          ("modi: 20,000 Modi trees len<=255 x 1,000,000 points, F=32, 8 outputs",
+                           W.modi(0), 8)):
+        t, v, s = api.population_to(prob.pop, dev)
+        X = torch.from_numpy(prob.X).to(dev)
+        ys = []
+        for k in range(prob.gt.pop):
+            gt_t, gt_v, gt_s = api.population_to(prob.gt.take([k]), dev)
+            gy, _ = api.tgp_eval_forward(gt_t, gt_v, gt_s, X, 1, max_len=prob.gt.max_len)
+            ys.append(gy[0, 0])
+        y = (torch.stack(ys, 1) + torch.from_numpy(prob.noise).to(dev)).contiguous()
+        g = torch.full((prob.pop.pop, O), 1.0 / prob.pop.pop, dtype=torch.float64, device=dev)
+        units = prob.pop.nodes() * prob.D
+        ms_f = _timed(lambda: api.tgp_fitness_mse(t, v, s, X, y, O, max_len=prob.pop.max_len), 1, 1)
+        ms_fb = _timed(lambda: api.tgp_eval_backward(t, v, s, X, y, g, O, max_len=prob.pop.max_len), 1, 1)
+        t_fp32, t_sfu = _roofline_time(prob.pop, prob.D, sms, f_hz, hbm_gbs, O)
+        line = {"workload": name + "; forward + adjoint", "node_points": units,
+                "ms_forward_mse": ms_f, "ms_forward_plus_adjoint": ms_fb,
+                "node_points_per_s_forward": units / (ms_f / 1e3),
+                "node_points_per_s_fwd_bwd": units / (ms_fb / 1e3),
+                "forward_roofline_frac": (max(t_fp32, t_sfu) * 1e3) / ms_f}
+        if O == 1:
+            const = (t == W.CONST)
+            idx = torch.zeros((prob.pop.pop, 16), dtype=torch.long, device=dev)
+            cnt = const.sum(1)
+            order = torch.argsort((~const).to(torch.int8), dim=1, stable=True)[:, :16]
+            mask = torch.arange(16, device=dev)[None, :] < cnt[:, None]
+            idx = torch.where(mask, order, torch.zeros_like(order))
+            consts = torch.gather(v, 1, idx).clone().requires_grad_(True)
+            opt = torch.optim.Adam([consts], lr=1e-2)
+
+            def adam_step():
+                val = v.scatter(1, idx, torch.where(mask, consts, torch.gather(v, 1, idx)))
+                mse = ag.fitness(val, X, t, s, y, 1, max_len=prob.pop.max_len)
+                loss = torch.nan_to_num(mse, nan=0.0, posinf=0.0).clamp(max=1e6).sum()
+                opt.zero_grad()
+                loss.backward()
+                consts.grad = torch.nan_to_num(consts.grad) * mask
+                opt.step()
+            line["ms_per_adam_step"] = _timed(adam_step, 20, 1)
+        out.append(line)
+    return out
+
+
 def main():
     a = _args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -384,6 +512,10 @@ def main():
     res = run_ours(a, rank, world, local_rank)
     if rank == 0 and res is not None:
         print(json.dumps(res), flush=True)
+        if a.suite:
+            import torch
+            for line in suite_lines(torch.device("cuda", local_rank), max(a.steps // 2, 2)):
+                print(json.dumps(line), flush=True)
     if world > 1:
         import torch
         torch.distributed.barrier()

@@ -104,9 +104,13 @@ bool choose_shape(long long P, long long D, int F, int O, int max_len, const tgp
     // small problems: fewer trees per block so that every SM gets work
     while (s.bt > 1 && cdiv(P, s.bt) * cdiv(Dr, s.tp) < target) s.bt /= 2;
   }
-  // fit shared memory (two CTAs per SM when possible)
+  // fit shared memory: two CTAs per SM (16 warps) when the heuristic picks
+  // the shape, the per-CTA maximum when the caller does
   const size_t limit = (size_t)dv.smem_optin;
+  const size_t two_per_sm = limit / 2 - 1024;
   auto bytes = [&]() { return eval_smem_bytes(s.K, s.nw, modi, mse, s.bt, pcap, s.tp, F, O); };
+  while (bytes() > two_per_sm && s.tp > CH && !(cfg && cfg->points_per_tile)) s.tp /= 2;
+  while (bytes() > two_per_sm && s.bt > 4 && !(cfg && cfg->trees_per_block)) s.bt /= 2;
   while (bytes() > limit && s.tp > CH && !(cfg && cfg->points_per_tile)) s.tp /= 2;
   while (bytes() > limit && s.bt > 1 && !(cfg && cfg->trees_per_block)) s.bt /= 2;
   if (bytes() > limit) return false;

@@ -1,0 +1,39 @@
+"""Multi-GPU sharding of the fitness path (host logic).
+
+The fitness of a population shards two ways without changing any result
+beyond rounding:
+  * by population: trees are independent, each rank evaluates a contiguous
+    range of trees (no exchange on the data path; `population_range`);
+  * by points: each rank evaluates every tree on a contiguous range of
+    points and the per-tree sums of squared residuals are added across
+    ranks (one all-reduce of pop * n_outputs doubles; `combine_point_shards`).
+The benchmark uses population replicas (weak scaling).  The point-sharded
+combination is what a rank-parallel caller of tgp_fitness_mse would run:
+    sse_r = mse_r * D_r;  SSE = all_reduce(sum, sse_r);  MSE = SSE / D.
+"""
+from __future__ import annotations
+
+
+def population_range(pop: int, rank: int, world: int) -> tuple[int, int]:
+    """Contiguous [start, stop) of trees owned by `rank` (sizes differ by <= 1)."""
+    base, rem = divmod(pop, world)
+    start = rank * base + min(rank, rem)
+    return start, start + base + (1 if rank < rem else 0)
+
+
+def point_range(n_points: int, rank: int, world: int) -> tuple[int, int]:
+    return population_range(n_points, rank, world)
+
+
+def combine_point_shards(mse_local, n_local: int, n_total: int, group=None):
+    """MSE over all points from each rank's MSE over its own points.
+
+    `mse_local` is a float64 tensor [pop, n_outputs] (NaN rows of invalid trees
+    stay NaN).  Uses one torch.distributed all_reduce (sum)."""
+    import torch
+    import torch.distributed as dist
+    sse = mse_local.to(torch.float64) * float(n_local)
+    if n_local == 0:
+        sse = torch.zeros_like(sse)
+    dist.all_reduce(sse, op=dist.ReduceOp.SUM, group=group)
+    return sse / float(n_total)

@@ -1,0 +1,59 @@
+"""Sharding of the fitness path across ranks, checked on CPU with the gloo
+backend (world size 2): population ranges partition the trees, and
+point-sharded MSEs combined by one all-reduce equal the unsharded MSE."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.multiprocessing as mp
+
+from paper_2501_17168_gb300 import shard, workloads as W
+
+
+def test_population_and_point_ranges_partition():
+    for n in (0, 1, 7, 100, 5001):
+        for world in (1, 2, 3, 8):
+            rs = [shard.population_range(n, r, world) for r in range(world)]
+            assert rs[0][0] == 0 and rs[-1][1] == n
+            assert all(a[1] == b[0] for a, b in zip(rs, rs[1:]))
+            sizes = [b - a for a, b in rs]
+            assert max(sizes) - min(sizes) <= 1
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, q):
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    torch.distributed.init_process_group("gloo", rank=rank, world_size=world)
+    prob = W.sr_small(3)
+    y = np.random.default_rng(0).standard_normal((prob.D, 1)).astype(np.float32)
+    a, b = shard.point_range(prob.D, rank, world)
+    m, _ = oracle.mse(prob.pop.type, prob.pop.val, prob.pop.size, prob.X[a:b], y[a:b], threads=1)
+    full = shard.combine_point_shards(torch.from_numpy(m), b - a, prob.D)
+    if rank == 0:
+        ref, _ = oracle.mse(prob.pop.type, prob.pop.val, prob.pop.size, prob.X, y, threads=1)
+        q.put(float(np.nanmax(np.abs(full.numpy() - ref) / np.maximum(np.abs(ref), 1e-300))))
+    torch.distributed.destroy_process_group()
+
+
+def test_point_sharded_mse_equals_unsharded():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    assert q.get(timeout=10) < 1e-12
