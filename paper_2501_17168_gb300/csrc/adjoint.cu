@@ -58,7 +58,7 @@ __host__ __device__ inline AdjSmem adj_smem_layout(int K, int nw, bool modi, int
 }
 
 template <int K, int NW, bool MODI, int CAP>
-__global__ void __launch_bounds__(NW * 32, 1) adjoint_kernel(AdjArgs a) {
+__global__ void __launch_bounds__(NW * 32, 2) adjoint_kernel(AdjArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int CH = 32 * K;
@@ -170,8 +170,8 @@ __global__ void __launch_bounds__(NW * 32, 1) adjoint_kernel(AdjArgs a) {
         }
         __syncwarp();
         bwd_reverse<K, MODI>(sm_addr(prog_w + (plen - 1)), sm_addr(prog_w), sm_addr(xs + qb),
-                             (unsigned)XS * 4u, sm_addr(gxs + qb), sm_addr(cg_w), sm_addr(sd_w + 4 * lane),
-                             tend, (unsigned)lane, seed);
+                             (unsigned)XS * 4u, sm_addr(gxs + ch * CH + lane), sm_addr(cg_w),
+                             sm_addr(sd_w + 4 * lane), tend, (unsigned)lane, seed);
         __syncwarp();
       }
       // flush the tree's constant gradients and squared residuals
@@ -192,7 +192,9 @@ __global__ void __launch_bounds__(NW * 32, 1) adjoint_kernel(AdjArgs a) {
     if (a.grad_X) {
       for (int i = tid; i < np * a.F; i += NW * 32) {
         const int q = i / a.F, f = i - (i / a.F) * a.F;
-        a.grad_X[(p0 + q) * a.F + f] += gxs[f * XS + q];
+        // tile layout [f][chunk][j][lane]: point q = chunk*CH + 4*lane + j
+        const int c = q / CH, r = q - c * CH;
+        a.grad_X[(p0 + q) * a.F + f] += gxs[f * XS + c * CH + (r & 3) * 32 + (r >> 2)];
       }
     }
     __syncthreads();

@@ -458,8 +458,9 @@ tgp_status run_backward(const tgp_population* pop, const tgp_data* data, const f
     int cap = 0;
     const void* fn = find_adj_kernel(K, nw, modi, pop->max_len, &cap);
     if (!fn) return TGP_ERR_UNSUPPORTED;
+    // tiles of 512 points, smaller when there are too few tiles for the GPU
     int tp = 512;
-    while (tp > 32 * K && (long long)(tp / 2) >= data->n_points) tp /= 2;
+    while (tp > 32 * K && cdiv(data->n_points, tp) < 2LL * dv.sms) tp /= 2;
     size_t smem = adj_smem_bytes(K, nw, modi, w.pcap, pop->max_len, tp, data->n_features, O);
     while (smem > (size_t)dv.smem_optin && tp > 32 * K) {
       tp /= 2;

@@ -319,11 +319,13 @@ class Rev(Base):
 
     # ---- accumulation targets
     def gx_add(self, vals):
-        """gradient tile of X at the lane's points of feature r_iy += vals"""
+        """gradient tile of X at the lane's points of feature r_iy += vals.
+        The tile is laid out [feature][chunk][j][lane] (r_gx already points
+        at the lane's word of the chunk), so the 32 lanes of one reduction
+        hit 32 different banks."""
         self.e("mad.lo.u32 r_ad, r_iy, r_xstr, r_gx;")
         for j in range(self.K):
-            off = 4 * j if j < 4 else 512 + 4 * (j - 4)
-            self.e(f"red.shared.add.f32 [r_ad+{off}], {vals(j)};")
+            self.e(f"red.shared.add.f32 [r_ad+{128 * j}], {vals(j)};")
 
     def gc_add(self, vals):
         """per-warp constant gradient [node] += sum over the warp's points"""
@@ -413,8 +415,8 @@ class Rev(Base):
         self.e("RLOOP:")
         self.e("mov.b32 r_ix, r_nx;")
         self.e("mov.b32 r_iy, r_ny;")
-        # prefetch the previous instruction (one below the program start reads
-        # the word before it; that word is never used)
+        # prefetch the previous instruction (below the program start this
+        # reads the pad word in front of it, which is never executed)
         self.e("ld.shared.v2.u32 {r_nx, r_ny}, [r_ptr+-8];")
         self.e("sub.u32 r_ptr, r_ptr, 8;")
         self.e("mov.b32 cv, r_iy;")
