@@ -28,7 +28,7 @@ __device__ __forceinline__ uint32_t sm_addr(const void* p) { return (uint32_t)__
 
 struct AdjSmem {
   size_t xs, gx, ys, warp, total;
-  size_t per_warp, w_prog, w_cg, w_mo, w_sd, w_g2;
+  size_t per_warp, w_prog, w_cg, w_mo, w_sd, w_g2, w_slot;
   int xs_stride;
 };
 
@@ -50,6 +50,7 @@ __host__ __device__ inline AdjSmem adj_smem_layout(int K, int nw, bool modi, int
   L.w_mo = w; w = al16(w + (modi ? (size_t)O * 32 * K * 4 : 0));
   L.w_sd = w; w = al16(w + (modi ? (size_t)O * 32 * K * 4 : 0));
   L.w_g2 = w; w = al16(w + (size_t)O * 4);
+  L.w_slot = w; w = al16(w + (size_t)R * 32 * K * 4);  // register-machine slots
   L.per_warp = w;
   L.warp = off; off = al16(off + (size_t)nw * w);
   off = al16(off + 64);  // item / tree counters
@@ -76,6 +77,7 @@ __global__ void __launch_bounds__(NW * 32, 2) adjoint_kernel(AdjArgs a) {
   float* mo_w = reinterpret_cast<float*>(wbase + lay.w_mo);
   float* sd_w = reinterpret_cast<float*>(wbase + lay.w_sd);
   float* g2_w = reinterpret_cast<float*>(wbase + lay.w_g2);
+  float* slot_w = reinterpret_cast<float*>(wbase + lay.w_slot);
   int* s_item = reinterpret_cast<int*>(smem + lay.total - 64);
   int* s_tree = s_item + 1;
   const int XS = lay.xs_stride;
@@ -137,7 +139,8 @@ __global__ void __launch_bounds__(NW * 32, 2) adjoint_kernel(AdjArgs a) {
         float acc[K];
         unsigned tend = tape_addr;
         const unsigned flag = bwd_forward<K, MODI>(sm_addr(prog_w), sm_addr(xs + qb), (unsigned)XS * 4u,
-                                                   sm_addr(mo_w + 4 * lane), tape_addr, acc, tend);
+                                                   sm_addr(mo_w + 4 * lane), tape_addr,
+                                                   sm_addr(slot_w + 4 * lane), acc, tend);
         float seed[K];
 #pragma unroll
         for (int j = 0; j < K; ++j) seed[j] = 0.0f;
@@ -171,7 +174,8 @@ __global__ void __launch_bounds__(NW * 32, 2) adjoint_kernel(AdjArgs a) {
         __syncwarp();
         bwd_reverse<K, MODI>(sm_addr(prog_w + (plen - 1)), sm_addr(prog_w), sm_addr(xs + qb),
                              (unsigned)XS * 4u, sm_addr(gxs + ch * CH + lane), sm_addr(cg_w),
-                             sm_addr(sd_w + 4 * lane), tend, (unsigned)lane, seed);
+                             sm_addr(sd_w + 4 * lane), tend, (unsigned)lane, sm_addr(slot_w + 4 * lane),
+                             seed);
         __syncwarp();
       }
       // flush the tree's constant gradients and squared residuals

@@ -458,20 +458,26 @@ tgp_status run_backward(const tgp_population* pop, const tgp_data* data, const f
     int cap = 0;
     const void* fn = find_adj_kernel(K, nw, modi, pop->max_len, &cap);
     if (!fn) return TGP_ERR_UNSUPPORTED;
-    // tiles of 512 points, smaller when there are too few tiles for the GPU
+    // A tile (every tree over tp points) is a large unit of work, so prefer
+    // enough tiles for several waves of the persistent grid: tiles of 512
+    // points, halved while there are fewer than 4 tiles per resident CTA.
     int tp = 512;
-    while (tp > 32 * K && cdiv(data->n_points, tp) < 2LL * dv.sms) tp /= 2;
-    size_t smem = adj_smem_bytes(K, nw, modi, w.pcap, pop->max_len, tp, data->n_features, O);
-    while (smem > (size_t)dv.smem_optin && tp > 32 * K) {
-      tp /= 2;
-      smem = adj_smem_bytes(K, nw, modi, w.pcap, pop->max_len, tp, data->n_features, O);
-    }
-    if (smem > (size_t)dv.smem_optin) return TGP_ERR_UNSUPPORTED;
-    if (!ensure_smem(fn, smem)) return TGP_ERR_CUDA;
+    size_t smem = 0;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nw * 32, smem) != cudaSuccess)
-      return TGP_ERR_CUDA;
-    if (per_sm < 1) return TGP_ERR_UNSUPPORTED;
+    for (;;) {
+      smem = adj_smem_bytes(K, nw, modi, w.pcap, pop->max_len, tp, data->n_features, O);
+      if (smem > (size_t)dv.smem_optin) {
+        if (tp <= 32 * K) return TGP_ERR_UNSUPPORTED;
+        tp /= 2;
+        continue;
+      }
+      if (!ensure_smem(fn, smem)) return TGP_ERR_CUDA;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nw * 32, smem) != cudaSuccess)
+        return TGP_ERR_CUDA;
+      if (per_sm < 1) return TGP_ERR_UNSUPPORTED;
+      if (tp <= 32 * K || cdiv(data->n_points, tp) >= 4LL * dv.sms * per_sm) break;
+      tp /= 2;
+    }
     AdjArgs a;
     a.prog = reinterpret_cast<const uint2*>(wsb + w.prog);
     a.plen = reinterpret_cast<const int*>(wsb + w.plen);

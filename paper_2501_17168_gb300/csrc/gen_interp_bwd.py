@@ -1,5 +1,8 @@
 """Generates interp_bwd.cuh: the two inline-PTX loops of the adjoint kernel.
 
+Both keep the eight slots in the warp's shared-memory slot area (one case
+per instruction family, the slot number taken from the opcode), which keeps
+the two loops small enough for the instruction cache.
 bwd_forward<K, MODI>  runs a compiled program like the forward interpreter
                       and, per instruction, appends the local partials the
                       reverse sweep will need to a per-thread tape in local
@@ -10,7 +13,7 @@ bwd_forward<K, MODI>  runs a compiled program like the forward interpreter
                         add/sub, leaves  nothing
 bwd_reverse<K, MODI>  walks the program from its last instruction to its
                       first with the adjoint of the accumulator in registers
-                      (G, K points per lane) and of the eight slots (GS), the
+                      (G, K points per lane) and of the eight slots, the
                       mirror image of the forward register machine: a slot
                       written by a spill in the forward is read back by that
                       spill's reverse, after the reverse of its consumer has
@@ -158,12 +161,12 @@ class Fwd(Base):
         K = self.K
         A, L, T, c = self.vec("A"), self.vec("L"), self.vec("T"), (lambda j: "cv")
         S = lambda d: (lambda j: f"S{d}_{j}")
-        regs = [f"{p}{j}" for p in "ALTVWM" for j in range(K)]
+        regs = [f"{p}{j}" for p in ("A", "L", "T", "V", "W", "M", "SV") for j in range(K)]
         self.e("{")
         self.e(".reg .f32 " + ", ".join(regs) + ", cv;")
-        self.e(".reg .f32 " + ", ".join(f"S{d}_{j}" for d in range(R) for j in range(K)) + ";")
         self.e(".reg .pred " + ", ".join(f"P{j}" for j in range(K)) + ";")
-        self.e(".reg .u32 r_ptr, r_ix, r_iy, r_nx, r_ny, r_op, r_ad, r_xc, r_xstr, r_mo, r_moo, r_ma, r_flag, r_tape;")
+        self.e(".reg .u32 r_ptr, r_ix, r_iy, r_nx, r_ny, r_op, r_ad, r_xc, r_xstr, r_mo, r_moo, r_ma, r_flag, r_tape, r_slot, r_d, r_sl;")
+        self.e("mov.u32 r_slot, %{slot};")
         self.e("mov.u32 r_ptr, %{pg};")
         self.e("mov.u32 r_xc, %{xc};")
         self.e("mov.u32 r_xstr, %{xstr};")
@@ -177,7 +180,7 @@ class Fwd(Base):
         self.e("add.u32 r_ptr, r_ptr, 8;")
         self.e("mov.b32 cv, r_iy;")
         self.e("and.b32 r_op, r_ix, 255;")
-        self.e("FTS: .branchtargets " + ", ".join(f"FC{k}" for k in range(OP_COUNT)) + ";")
+        self.e("FTS: .branchtargets " + ", ".join(fwd_label(k) for k in range(OP_COUNT)) + ";")
         self.e("brx.idx.uni r_op, FTS;")
         self.e(f"FC{OP_END_ROOT}:")
         self.e("mov.u32 r_flag, 0;")
@@ -258,48 +261,69 @@ class Fwd(Base):
             self.case(OP_RC + f, rc)
             for op, fn in ((OP_BV_M, bv), (OP_BC_M, bc), (OP_RV_M, rv), (OP_RC_M, rc)):
                 self.case(op + f, (lambda fn=fn: fn(modi=True)) if self.modi else (lambda: None))
-        for d in range(R):
-            def spv(d=d):
-                for j in range(K):
-                    self.e(f"mov.f32 S{d}_{j}, A{j};")
-                self.load_x(A)
+        # slots live in the warp's shared-memory slot area ([R][32 lanes][K]);
+        # one case per family, the slot index comes from the opcode
+        def slot_addr(base):
+            self.e(f"sub.u32 r_d, r_op, {base};")
+            self.e(f"mad.lo.u32 r_sl, r_d, {128 * K}, r_slot;")
 
-            def spc(d=d):
-                for j in range(K):
-                    self.e(f"mov.f32 S{d}_{j}, A{j};")
-                    self.e(f"mov.f32 A{j}, cv;")
+        def st_slot(src):
+            for h in range(K // 4):
+                regs = ", ".join(src(4 * h + q) for q in range(4))
+                self.e(f"st.shared.v4.f32 [r_sl+{512 * h}], {{{regs}}};")
 
-            self.case(OP_SPV + d, spv)
-            self.case(OP_SPC + d, spc)
+        def ld_slot(dst):
+            for h in range(K // 4):
+                regs = ", ".join(dst(4 * h + q) for q in range(4))
+                self.e(f"ld.shared.v4.f32 {{{regs}}}, [r_sl+{512 * h}];")
+
+        SV = self.vec("SV")
+        self.e("FSPV:")
+        slot_addr(OP_SPV)
+        st_slot(A)
+        self.load_x(A)
+        self.e("bra.uni FLOOP;")
+        self.e("FSPC:")
+        slot_addr(OP_SPC)
+        st_slot(A)
+        for j in range(K):
+            self.e(f"mov.f32 A{j}, cv;")
+        self.e("bra.uni FLOOP;")
         for f in BIN:
             need = f in NEEDS_OPERAND
-            for d in range(R):
-                def bs(f=f, d=d, need=need, modi=False):
-                    if need:
-                        self.tape_put(S(d))
-                        self.tape_put(A)
-                    if modi:
-                        self.fn2(f, T, S(d), A)
-                        self.modi_add(T)
-                    else:
-                        self.fn2(f, A, S(d), A)
 
-                def rs(f=f, d=d, need=need, modi=False):
-                    if need:
-                        self.tape_put(S(d))
-                        self.tape_put(A)
-                    if modi:
-                        self.fn2(f, T, A, S(d))
-                        self.modi_add(T)
-                        for j in range(K):
-                            self.e(f"mov.f32 A{j}, S{d}_{j};")
-                    else:
-                        self.fn2(f, A, A, S(d))
+            def bs(f=f, need=need, modi=False, base=None):
+                slot_addr(base)
+                ld_slot(SV)
+                if need:
+                    self.tape_put(SV)
+                    self.tape_put(A)
+                if modi:
+                    self.fn2(f, T, SV, A)
+                    self.modi_add(T)
+                else:
+                    self.fn2(f, A, SV, A)
 
-                self.case(OP_BS + f * R + d, bs)
-                self.case(OP_RS + f * R + d, rs)
-                self.case(OP_BS_M + f * R + d, (lambda bs=bs: bs(modi=True)) if self.modi else (lambda: None))
-                self.case(OP_RS_M + f * R + d, (lambda rs=rs: rs(modi=True)) if self.modi else (lambda: None))
+            def rs(f=f, need=need, modi=False, base=None):
+                slot_addr(base)
+                ld_slot(SV)
+                if need:
+                    self.tape_put(SV)
+                    self.tape_put(A)
+                if modi:
+                    self.fn2(f, T, A, SV)
+                    self.modi_add(T)
+                    for j in range(K):
+                        self.e(f"mov.f32 A{j}, SV{j};")
+                else:
+                    self.fn2(f, A, A, SV)
+
+            for lab, fn, base, modi in ((f"FBS{f}", bs, OP_BS + f * R, False), (f"FRS{f}", rs, OP_RS + f * R, False),
+                                        (f"FBSM{f}", bs, OP_BS_M + f * R, True), (f"FRSM{f}", rs, OP_RS_M + f * R, True)):
+                self.e(f"{lab}:")
+                if not modi or self.modi:
+                    fn(modi=modi, base=base)
+                self.e("bra.uni FLOOP;")
         self.e("FDONE:")
         for j in range(K):
             self.e(f"mov.f32 %{{a{j}}}, A{j};")
@@ -393,12 +417,12 @@ class Rev(Base):
         DA, DB, SD = self.vec("DA"), self.vec("DB"), self.vec("SD")
         GS = lambda d: (lambda j: f"GS{d}_{j}")
         c = lambda j: "cv"
-        regs = [f"{p}{j}" for p in ("G", "L", "T", "U", "V", "W", "DA", "DB", "SD") for j in range(K)]
+        regs = [f"{p}{j}" for p in ("G", "L", "T", "U", "V", "W", "DA", "DB", "SD", "GSV") for j in range(K)]
         self.e("{")
         self.e(".reg .f32 " + ", ".join(regs) + ", cv, q_s, q_t;")
-        self.e(".reg .f32 " + ", ".join(f"GS{d}_{j}" for d in range(R) for j in range(K)) + ";")
         self.e(".reg .pred " + ", ".join([f"P{j}" for j in range(K)] + [f"Q{j}" for j in range(K)]) + ", PL;")
-        self.e(".reg .u32 r_ptr, r_ix, r_iy, r_nx, r_ny, r_op, r_ad, r_xc, r_xstr, r_gx, r_cg, r_sd, r_moo, r_ma, r_tape, r_nd, r_ca, r_lane, r_beg;")
+        self.e(".reg .u32 r_ptr, r_ix, r_iy, r_nx, r_ny, r_op, r_ad, r_xc, r_xstr, r_gx, r_cg, r_sd, r_moo, r_ma, r_tape, r_nd, r_ca, r_lane, r_beg, r_slot, r_d, r_sl;")
+        self.e("mov.u32 r_slot, %{slot};")
         self.e("mov.u32 r_ptr, %{plast};")
         self.e("mov.u32 r_beg, %{pg};")
         self.e("mov.u32 r_xc, %{xc};")
@@ -421,7 +445,7 @@ class Rev(Base):
         self.e("sub.u32 r_ptr, r_ptr, 8;")
         self.e("mov.b32 cv, r_iy;")
         self.e("and.b32 r_op, r_ix, 255;")
-        self.e("RTR: .branchtargets " + ", ".join(f"RC{k}" for k in range(OP_COUNT)) + ";")
+        self.e("RTR: .branchtargets " + ", ".join(rev_label(k) for k in range(OP_COUNT)) + ";")
         self.e("brx.idx.uni r_op, RTR;")
 
         # the program's terminator starts the sweep: the root's adjoint (END_ROOT)
@@ -557,66 +581,108 @@ class Rev(Base):
             for op, fn in ((OP_BV_M, bvm), (OP_BC_M, bcm), (OP_RV_M, rvm), (OP_RC_M, rcm)):
                 self.case(op + f, fn if self.modi else (lambda: None))
 
-        for d in range(R):
-            def spv(d=d):
-                self.gx_add(G)
-                for j in range(K):
-                    self.e(f"mov.f32 G{j}, GS{d}_{j};")
+        def slot_addr(base):
+            self.e(f"sub.u32 r_d, r_op, {base};")
+            self.e(f"mad.lo.u32 r_sl, r_d, {128 * K}, r_slot;")
 
-            def spc(d=d):
-                self.gc_add(G)
-                for j in range(K):
-                    self.e(f"mov.f32 G{j}, GS{d}_{j};")
+        def st_slot(src):
+            for h in range(K // 4):
+                regs = ", ".join(src(4 * h + q) for q in range(4))
+                self.e(f"st.shared.v4.f32 [r_sl+{512 * h}], {{{regs}}};")
 
-            self.case(OP_SPV + d, spv)
-            self.case(OP_SPC + d, spc)
+        def ld_slot(dst):
+            for h in range(K // 4):
+                regs = ", ".join(dst(4 * h + q) for q in range(4))
+                self.e(f"ld.shared.v4.f32 {{{regs}}}, [r_sl+{512 * h}];")
 
+        GSV = self.vec("GSV")
+        self.e("RSPV:")
+        slot_addr(OP_SPV)
+        self.gx_add(G)
+        ld_slot(G)
+        self.e("bra.uni RLOOP;")
+        self.e("RSPC:")
+        slot_addr(OP_SPC)
+        self.gc_add(G)
+        ld_slot(G)
+        self.e("bra.uni RLOOP;")
         for f in BIN:
             need = f in NEEDS_OPERAND
-            for d in range(R):
-                # BS: acc = f(a = s[d], b = acc_before); tape: s[d] then acc
-                def bs(f=f, d=d, need=need):
-                    if need:
-                        self.tape_get(T2)        # acc_before (b)
-                        self.tape_get(T1)        # s[d] (a)
-                    self.dfn2(f, T1, T2, G, GS(d), DB)
-                    for j in range(K):
-                        self.e(f"mov.f32 G{j}, DB{j};")
 
-                # RS: acc = f(a = acc_before, b = s[d])
-                def rs(f=f, d=d, need=need):
-                    if need:
-                        self.tape_get(T2)        # acc_before (a)
-                        self.tape_get(T1)        # s[d] (b)
-                    self.dfn2(f, T2, T1, G, DA, GS(d))
-                    for j in range(K):
-                        self.e(f"mov.f32 G{j}, DA{j};")
+            def bs(f=f, need=need):
+                if need:
+                    self.tape_get(T2)        # acc_before (b)
+                    self.tape_get(T1)        # s[d] (a)
+                self.dfn2(f, T1, T2, G, GSV, DB)
+                st_slot(GSV)
+                for j in range(K):
+                    self.e(f"mov.f32 G{j}, DB{j};")
 
-                def bsm(f=f, d=d, need=need):   # out += f(s[d], acc); acc unchanged
-                    if need:
-                        self.tape_get(T2)
-                        self.tape_get(T1)
-                    self.seed(SD)
-                    self.dfn2(f, T1, T2, SD, GS(d), DB)
-                    self.addv(G, G, DB)
+            def rs(f=f, need=need):
+                if need:
+                    self.tape_get(T2)        # acc_before (a)
+                    self.tape_get(T1)        # s[d] (b)
+                self.dfn2(f, T2, T1, G, DA, GSV)
+                st_slot(GSV)
+                for j in range(K):
+                    self.e(f"mov.f32 G{j}, DA{j};")
 
-                def rsm(f=f, d=d, need=need):   # out += f(acc, s[d]); acc = s[d]
-                    if need:
-                        self.tape_get(T2)
-                        self.tape_get(T1)
-                    self.seed(SD)
-                    self.dfn2(f, T2, T1, SD, DA, DB)
-                    self.addv(GS(d), DB, G)
-                    for j in range(K):
-                        self.e(f"mov.f32 G{j}, DA{j};")
+            def bsm(f=f, need=need):         # out += f(s[d], acc); acc unchanged
+                if need:
+                    self.tape_get(T2)
+                    self.tape_get(T1)
+                self.seed(SD)
+                self.dfn2(f, T1, T2, SD, GSV, DB)
+                st_slot(GSV)
+                self.addv(G, G, DB)
 
-                self.case(OP_BS + f * R + d, bs)
-                self.case(OP_RS + f * R + d, rs)
-                self.case(OP_BS_M + f * R + d, bsm if self.modi else (lambda: None))
-                self.case(OP_RS_M + f * R + d, rsm if self.modi else (lambda: None))
+            def rsm(f=f, need=need):         # out += f(acc, s[d]); acc = s[d]
+                if need:
+                    self.tape_get(T2)
+                    self.tape_get(T1)
+                self.seed(SD)
+                self.dfn2(f, T2, T1, SD, DA, DB)
+                self.addv(GSV, DB, G)
+                st_slot(GSV)
+                for j in range(K):
+                    self.e(f"mov.f32 G{j}, DA{j};")
+
+            for lab, fn, base, modi in ((f"RBS{f}", bs, OP_BS + f * R, False), (f"RRS{f}", rs, OP_RS + f * R, False),
+                                        (f"RBSM{f}", bsm, OP_BS_M + f * R, True), (f"RRSM{f}", rsm, OP_RS_M + f * R, True)):
+                self.e(f"{lab}:")
+                if not modi or self.modi:
+                    slot_addr(base)
+                    fn()
+                self.e("bra.uni RLOOP;")
         self.e("RDONE:")
         self.e("}")
         return "\n".join(self.lines)
+
+
+def _family(k):
+    """(family, f) of a slot-indexed opcode, or None"""
+    if OP_SPV <= k < OP_SPV + R:
+        return ("SPV", None)
+    if OP_SPC <= k < OP_SPC + R:
+        return ("SPC", None)
+    for base, name in ((OP_BS, "BS"), (OP_RS, "RS"), (OP_BS_M, "BSM"), (OP_RS_M, "RSM")):
+        if base <= k < base + 5 * R:
+            return (name, (k - base) // R)
+    return None
+
+
+def fwd_label(k):
+    fam = _family(k)
+    if fam is None:
+        return f"FC{k}"
+    return f"F{fam[0]}" + ("" if fam[1] is None else str(fam[1]))
+
+
+def rev_label(k):
+    fam = _family(k)
+    if fam is None:
+        return f"RC{k}"
+    return f"R{fam[0]}" + ("" if fam[1] is None else str(fam[1]))
 
 
 def _literal(body: str) -> str:
@@ -626,19 +692,19 @@ def _literal(body: str) -> str:
 
 def render_fwd(K, modi):
     body = Fwd(K, modi).build()
-    names = [f"a{j}" for j in range(K)] + ["flag", "tend", "pg", "xc", "xstr", "mo", "tape"]
+    names = [f"a{j}" for j in range(K)] + ["flag", "tend", "pg", "xc", "xstr", "mo", "tape", "slot"]
     for i, n in enumerate(names):
         body = body.replace("%{" + n + "}", f"%{i}")
     outs = ", ".join([f'"=f"(acc[{j}])' for j in range(K)] + ['"=r"(flag)', '"=r"(tend)'])
     return f"""template <>
 __device__ __forceinline__ unsigned bwd_forward<{K}, {'true' if modi else 'false'}>(
-    unsigned pg, unsigned xc, unsigned xstr, unsigned mo, unsigned tape, float (&acc)[{K}],
-    unsigned& tend) {{
+    unsigned pg, unsigned xc, unsigned xstr, unsigned mo, unsigned tape, unsigned slot,
+    float (&acc)[{K}], unsigned& tend) {{
   unsigned flag;
   asm volatile(
 {_literal(body)}
       : {outs}
-      : "r"(pg), "r"(xc), "r"(xstr), "r"(mo), "r"(tape)
+      : "r"(pg), "r"(xc), "r"(xstr), "r"(mo), "r"(tape), "r"(slot)
       : "memory");
   return flag;
 }}
@@ -647,15 +713,15 @@ __device__ __forceinline__ unsigned bwd_forward<{K}, {'true' if modi else 'false
 
 def render_rev(K, modi):
     body = Rev(K, modi).build()
-    names = ["plast", "pg", "xc", "xstr", "gx", "cg", "sd", "tend", "lane"] + [f"s{j}" for j in range(K)]
+    names = ["plast", "pg", "xc", "xstr", "gx", "cg", "sd", "tend", "lane", "slot"] + [f"s{j}" for j in range(K)]
     for i, n in enumerate(names):
         body = body.replace("%{" + n + "}", f"%{i}")
     ins = ", ".join(['"r"(plast)', '"r"(pg)', '"r"(xc)', '"r"(xstr)', '"r"(gx)', '"r"(cg)', '"r"(sd)',
-                     '"r"(tend)', '"r"(lane)'] + [f'"f"(seed[{j}])' for j in range(K)])
+                     '"r"(tend)', '"r"(lane)', '"r"(slot)'] + [f'"f"(seed[{j}])' for j in range(K)])
     return f"""template <>
 __device__ __forceinline__ void bwd_reverse<{K}, {'true' if modi else 'false'}>(
     unsigned plast, unsigned pg, unsigned xc, unsigned xstr, unsigned gx, unsigned cg, unsigned sd,
-    unsigned tend, unsigned lane, const float (&seed)[{K}]) {{
+    unsigned tend, unsigned lane, unsigned slot, const float (&seed)[{K}]) {{
   asm volatile(
 {_literal(body)}
       :
@@ -673,13 +739,13 @@ def main():
         "namespace tgp {",
         "template <int K, bool MODI>",
         "__device__ __forceinline__ unsigned bwd_forward(unsigned pg, unsigned xc, unsigned xstr,",
-        "                                                unsigned mo, unsigned tape, float (&acc)[K],",
-        "                                                unsigned& tend);",
+        "                                                unsigned mo, unsigned tape, unsigned slot,",
+        "                                                float (&acc)[K], unsigned& tend);",
         "template <int K, bool MODI>",
         "__device__ __forceinline__ void bwd_reverse(unsigned plast, unsigned pg, unsigned xc,",
         "                                            unsigned xstr, unsigned gx, unsigned cg,",
         "                                            unsigned sd, unsigned tend, unsigned lane,",
-        "                                            const float (&seed)[K]);",
+        "                                            unsigned slot, const float (&seed)[K]);",
     ]
     for K, modi in ((4, False), (4, True)):
         parts.append(render_fwd(K, modi))
