@@ -431,26 +431,72 @@ def suite_lines(dev, steps):
             api.tgp_fitness_mse(tt, vv, ss, Xp, yp, 1, max_len=bp.pop.max_len, mse=bp.mse,
                                 tree_status=bp.status)
     ms_each = _timed(per_problem, steps, 2)
-    n = api.tgp_batch_workspace_size(bps)
+    # autotuned schedule: every problem gets its measured-best launch shape
+    # (points per lane fixed at 8 so that one launch serves all of them)
+    from paper_2501_17168_gb300 import autotune
+    tuned = []
+    for bp in bps:
+        tt, vv, ss, Xp, yp = bp.tensors
+        cands = [c for c in autotune.candidates(bp.pop.pop, bp.data.n_points, 1)
+                 if c["points_per_lane"] == 8 and c["trees_per_block"] >= 4]
+        best, _ = autotune.tune(tt, vv, ss, Xp, yp, 1, max_len=bp.pop.max_len, reps=2, cands=cands,
+                                store=False)
+        tuned.append(api.BatchProblem(tt, vv, ss, Xp, yp, 1, max_len=bp.pop.max_len, config=best))
+    ms_tuned = _timed(lambda: api.tgp_batch_fitness_mse(tuned), steps, 2)
+    n = api.tgp_batch_workspace_size(tuned)
     ws = torch.empty(n, dtype=torch.uint8, device=dev)
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        api.tgp_batch_fitness_mse(tuned, ws=ws)
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        api.tgp_batch_fitness_mse(tuned, ws=ws)
+    ms_graph = _timed(graph.replay, steps, 2)
+    out.append({"workload": "batched_uneven: 8 problems, P 2,990-19,622, D 3,122-381,279, F 5-30, "
+                            "len U[7,511]; forward + MSE",
+                "node_points": units, "ms_batched_heuristic": ms_batch,
+                "ms_batched_autotuned": ms_tuned, "ms_graph_replay_autotuned": ms_graph,
+                "ms_one_launch_per_problem": ms_each,
+                "node_points_per_s_graph": units / (ms_graph / 1e3),
+                "node_points_per_s_per_problem": units / (ms_each / 1e3),
+                "speedup_graph_vs_per_problem": ms_each / ms_graph,
+                "roofline_frac_graph": (t_sfu * 1e3) / ms_graph,
+                "configs": [{k: v for k, v in tp.cfg.__class__.__dict__.items() if False} or
+                            {f: getattr(tp.cfg, f) for f in ("trees_per_block", "points_per_tile",
+                                                            "tiles_per_item", "points_per_lane")}
+                            for tp in tuned]})
+
+    # many small problems (each too small to fill the GPU on its own)
+    probs = W.batched_uneven(7, n_problems=16, pop_range=(500, 2000), d_range=(500, 5000))
+    bps, units = [], 0.0
+    for pr in probs:
+        tt, vv, ss = api.population_to(pr.pop, dev)
+        Xp, yp = _gpu_targets(api, pr, dev)
+        bps.append(api.BatchProblem(tt, vv, ss, Xp, yp, 1, max_len=pr.pop.max_len))
+        units += pr.pop.nodes() * pr.D
+    n = api.tgp_batch_workspace_size(bps)
+    ws = torch.empty(n, dtype=torch.uint8, device=dev)
     with torch.cuda.stream(side):
         api.tgp_batch_fitness_mse(bps, ws=ws)
     torch.cuda.current_stream().wait_stream(side)
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
         api.tgp_batch_fitness_mse(bps, ws=ws)
-    ms_graph = _timed(graph.replay, steps, 2)
-    out.append({"workload": "batched_uneven: 8 problems, P 2,990-19,622, D 3,122-381,279, F 5-30, "
+    ms_graph = _timed(graph.replay, 20, 3)
+
+    def per_problem_small():
+        for bp in bps:
+            tt, vv, ss, Xp, yp = bp.tensors
+            api.tgp_fitness_mse(tt, vv, ss, Xp, yp, 1, max_len=bp.pop.max_len, mse=bp.mse,
+                                tree_status=bp.status)
+    ms_each = _timed(per_problem_small, 20, 3)
+    out.append({"workload": "batched_small: 16 problems, P U{500..2000}, D log-U[500, 5000], F 4-32, "
                             "len U[7,511]; forward + MSE",
-                "node_points": units, "ms_batched": ms_batch, "ms_graph_replay": ms_graph,
-                "ms_one_launch_per_problem": ms_each,
-                "node_points_per_s_batched": units / (ms_batch / 1e3),
-                "node_points_per_s_graph": units / (ms_graph / 1e3),
-                "node_points_per_s_per_problem": units / (ms_each / 1e3),
-                "speedup_vs_per_problem": ms_each / ms_batch,
-                "roofline_frac_graph": (t_sfu * 1e3) / ms_graph})
+                "node_points": units, "ms_graph_replay": ms_graph, "ms_one_launch_per_problem": ms_each,
+                "speedup_graph_vs_per_problem": ms_each / ms_graph,
+                "node_points_per_s_graph": units / (ms_graph / 1e3)})
 
     # differentiation: forward MSE, fused forward + adjoint, one Adam step
     for name, prob, O in (("diff: 10,000 trees len<=127 (<=16 constants) x 200,000 points, F=4",
