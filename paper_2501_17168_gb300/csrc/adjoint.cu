@@ -59,7 +59,7 @@ __host__ __device__ inline AdjSmem adj_smem_layout(int K, int nw, bool modi, int
 }
 
 template <int K, int NW, bool MODI, int CAP>
-__global__ void __launch_bounds__(NW * 32, 2) adjoint_kernel(AdjArgs a) {
+__global__ void __launch_bounds__(NW * 32, 3) adjoint_kernel(AdjArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int CH = 32 * K;

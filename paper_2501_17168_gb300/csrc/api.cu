@@ -23,6 +23,7 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 constexpr int kNW = 8;
+constexpr int kCtasPerSm = 3;  // resident evaluation CTAs the shape heuristic aims for
 
 struct DevInfo {
   bool init = false;
@@ -104,13 +105,13 @@ bool choose_shape(long long P, long long D, int F, int O, int max_len, const tgp
     // small problems: fewer trees per block so that every SM gets work
     while (s.bt > 1 && cdiv(P, s.bt) * cdiv(Dr, s.tp) < target) s.bt /= 2;
   }
-  // fit shared memory: two CTAs per SM (16 warps) when the heuristic picks
-  // the shape, the per-CTA maximum when the caller does
+  // fit shared memory: kCtasPerSm CTAs per SM when the heuristic picks the
+  // shape, the per-CTA maximum when the caller does
   const size_t limit = (size_t)dv.smem_optin;
-  const size_t two_per_sm = limit / 2 - 1024;
+  const size_t per_cta = limit / kCtasPerSm - 1024;
   auto bytes = [&]() { return eval_smem_bytes(s.K, s.nw, modi, mse, s.bt, pcap, s.tp, F, O); };
-  while (bytes() > two_per_sm && s.tp > CH && !(cfg && cfg->points_per_tile)) s.tp /= 2;
-  while (bytes() > two_per_sm && s.bt > 4 && !(cfg && cfg->trees_per_block)) s.bt /= 2;
+  while (bytes() > per_cta && s.tp > CH && !(cfg && cfg->points_per_tile)) s.tp /= 2;
+  while (bytes() > per_cta && s.bt > 4 && !(cfg && cfg->trees_per_block)) s.bt /= 2;
   while (bytes() > limit && s.tp > CH && !(cfg && cfg->points_per_tile)) s.tp /= 2;
   while (bytes() > limit && s.bt > 1 && !(cfg && cfg->trees_per_block)) s.bt /= 2;
   if (bytes() > limit) return false;

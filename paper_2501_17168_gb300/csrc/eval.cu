@@ -126,7 +126,7 @@ __host__ __device__ inline EvalSmem eval_smem_layout(int K, int nw, bool modi, b
 
 // ----------------------------------------------------------- kernel
 template <int K, int NW, bool MODI, bool OUT>
-__global__ void __launch_bounds__(NW * 32, 2) eval_kernel(const __grid_constant__ EvalBatch b) {
+__global__ void __launch_bounds__(NW * 32, 3) eval_kernel(const __grid_constant__ EvalBatch b) {
   extern __shared__ __align__(16) unsigned char smem_all[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int CH = 32 * K;
