@@ -164,11 +164,13 @@ size_t tgp_batch_workspace_size(const tgp_problem* probs, int32_t n);
 
 /* SR fitness of n independent problems of uneven sizes (populations, tree
  * lengths, point counts, feature counts) in one stage launch, one persistent
- * evaluation launch and one finalize launch (two evaluation launches when
- * single-output and Modi populations are mixed).  The persistent CTAs pull
- * work items of every problem from one counter, so small and large problems
- * fill the GPU together.  Same per-problem results as tgp_fitness_mse.  All
- * problems with one output must use the same points_per_lane.  Legal in
+ * evaluation launch per occupancy group and one finalize launch.  Problems
+ * whose shared-memory footprint allows the same number of CTAs per SM form a
+ * group (at most three groups, doubled when single-output and Modi
+ * populations are mixed); within a group the persistent CTAs pull work items
+ * of every problem from one counter, so small and large problems fill the
+ * GPU together.  Same per-problem results as tgp_fitness_mse.  All problems
+ * with one output must use the same points_per_lane.  Legal in
  * stream capture (the batched call of one generation is a CUDA graph). */
 tgp_status tgp_batch_fitness_mse(const tgp_problem* probs, int32_t n, void* ws, size_t ws_bytes,
                                  void* stream);

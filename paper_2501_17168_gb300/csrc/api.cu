@@ -108,10 +108,21 @@ bool choose_shape(long long P, long long D, int F, int O, int max_len, const tgp
   // fit shared memory: kCtasPerSm CTAs per SM when the heuristic picks the
   // shape, the per-CTA maximum when the caller does
   const size_t limit = (size_t)dv.smem_optin;
-  const size_t per_cta = limit / kCtasPerSm - 1024;
   auto bytes = [&]() { return eval_smem_bytes(s.K, s.nw, modi, mse, s.bt, pcap, s.tp, F, O); };
-  while (bytes() > per_cta && s.tp > CH && !(cfg && cfg->points_per_tile)) s.tp /= 2;
-  while (bytes() > per_cta && s.bt > 4 && !(cfg && cfg->trees_per_block)) s.bt /= 2;
+  {
+    // three CTAs per SM when that keeps tiles of >= 2 chunks and blocks of
+    // >= 8 trees, else two (wide X tiles, long programs, Modi accumulators)
+    const Shape s0 = s;
+    bool fit = false;
+    for (int ctas = kCtasPerSm; ctas >= 2 && !fit; --ctas) {
+      s = s0;
+      const size_t per_cta = limit / ctas - 1024;
+      const int tp_min = ctas > 2 ? 2 * CH : CH, bt_min = ctas > 2 ? 8 : 4;
+      while (bytes() > per_cta && s.tp > tp_min && !(cfg && cfg->points_per_tile)) s.tp /= 2;
+      while (bytes() > per_cta && s.bt > bt_min && !(cfg && cfg->trees_per_block)) s.bt /= 2;
+      fit = bytes() <= per_cta;
+    }
+  }
   while (bytes() > limit && s.tp > CH && !(cfg && cfg->points_per_tile)) s.tp /= 2;
   while (bytes() > limit && s.bt > 1 && !(cfg && cfg->trees_per_block)) s.bt /= 2;
   if (bytes() > limit) return false;
@@ -201,7 +212,8 @@ tgp_status plan(Planned& q, const tgp_config* cfg, bool mse, const DevInfo& dv) 
   return TGP_OK;
 }
 
-tgp_status launch_stage(Planned* qs, int n, char* ws, cudaStream_t st, const DevInfo& dv) {
+tgp_status launch_stage(Planned* qs, int n, char* ws, cudaStream_t st, const DevInfo& dv,
+                        bool want_nodes = false) {
   StageBatch b{};
   long long total = 0;
   int m = 0;
@@ -224,6 +236,7 @@ tgp_status launch_stage(Planned* qs, int n, char* ws, cudaStream_t st, const Dev
     a.status = reinterpret_cast<int*>(w + q.w.status);
     a.user_status = q.status_out;
     a.ctrl = reinterpret_cast<unsigned*>(w + q.w.ctrl);
+    a.want_nodes = want_nodes ? 1 : 0;
     total += q.pop->pop;
     b.end[m] = total;
     ++m;
@@ -244,71 +257,81 @@ tgp_status launch_stage(Planned* qs, int n, char* ws, cudaStream_t st, const Dev
 
 // Launches the evaluation kernels over every problem's work items (the plain
 // variant only when some problem has a single output; each variant skips the
-// items of problems whose Modi flag does not match it).
+// items of problems whose Modi flag does not match it).  Problems are grouped
+// by how many CTAs of their shared-memory footprint fit on an SM, and each
+// group gets one persistent launch sized for that occupancy, so a problem
+// with wide tiles does not lower the occupancy of the others.
 tgp_status launch_eval(Planned* qs, int n, char* ws, unsigned* counters, cudaStream_t st,
                        const DevInfo& dv, bool mse) {
   bool any_single = false;
   for (int i = 0; i < n; ++i) any_single |= qs[i].O == 1;
+  const size_t limit = (size_t)dv.smem_optin;
   for (int variant = 0; variant < 2; ++variant) {
     const bool modi = variant == 1;
     if (!modi && !any_single) continue;
-    EvalBatch b{};
-    b.counter = counters + (modi ? CTRL_COUNTER_MODI : CTRL_COUNTER);
-    long long total = 0;
-    size_t smem = 0;
-    int K = 0, nw = 0, m = 0;
-    for (int i = 0; i < n; ++i) {
-      const Planned& q = qs[i];
-      if (q.pop->pop == 0 || q.data->n_points == 0) continue;
-      if (!modi && q.O > 1) continue;
-      const Shape& sh = modi ? q.sm : q.sp;
-      if (m > 0 && (sh.K != K || sh.nw != nw)) return TGP_ERR_UNSUPPORTED;
-      K = sh.K;
-      nw = sh.nw;
-      char* w = ws + q.base;
-      EvalArgs& a = b.p[m];
-      a.prog = reinterpret_cast<const uint2*>(w + q.w.prog);
-      a.plen = reinterpret_cast<const int*>(w + q.w.plen);
-      a.status = reinterpret_cast<const int*>(w + q.w.status);
-      a.pcap = q.w.pcap;
-      a.pop = q.pop->pop;
-      a.X = q.data->X;
-      a.D = q.data->n_points;
-      a.F = q.data->n_features;
-      a.ldx = q.data->ldx;
-      a.y = q.y;
-      a.O = q.O;
-      a.out = q.out;
-      a.partial = reinterpret_cast<double*>(w + q.w.partial);
-      a.bt = sh.bt;
-      a.tp = sh.tp;
-      a.g = sh.g;
-      a.n_tiles = sh.n_tiles;
-      a.n_groups = sh.n_groups;
-      a.n_blocks = sh.n_blocks;
-      a.n_items = sh.n_items;
-      a.ctrl = reinterpret_cast<unsigned*>(w + q.w.ctrl);
-      total += sh.n_items;
-      b.end[m] = total;
-      size_t sb = eval_smem_bytes(sh.K, sh.nw, modi, mse, sh.bt, q.w.pcap, sh.tp, q.data->n_features, q.O);
-      if (sb > smem) smem = sb;
-      ++m;
+    for (int cls = kCtasPerSm; cls >= 1; --cls) {
+      const size_t lo = cls < kCtasPerSm ? limit / (cls + 1) - 1024 : 0;
+      const size_t hi = cls > 1 ? limit / cls - 1024 : limit;
+      EvalBatch b{};
+      b.counter = counters + CTRL_COUNTER_GROUP + 2 * (kCtasPerSm - cls) + (modi ? 1 : 0);
+      long long total = 0;
+      size_t smem = 0;
+      int K = 0, nw = 0, m = 0;
+      for (int i = 0; i < n; ++i) {
+        const Planned& q = qs[i];
+        if (q.pop->pop == 0 || q.data->n_points == 0) continue;
+        if (!modi && q.O > 1) continue;
+        const Shape& sh = modi ? q.sm : q.sp;
+        const size_t sb =
+            eval_smem_bytes(sh.K, sh.nw, modi, mse, sh.bt, q.w.pcap, sh.tp, q.data->n_features, q.O);
+        if (!(sb > lo && sb <= hi)) continue;
+        if (m > 0 && (sh.K != K || sh.nw != nw)) return TGP_ERR_UNSUPPORTED;
+        K = sh.K;
+        nw = sh.nw;
+        char* w = ws + q.base;
+        EvalArgs& a = b.p[m];
+        a.prog = reinterpret_cast<const uint2*>(w + q.w.prog);
+        a.plen = reinterpret_cast<const int*>(w + q.w.plen);
+        a.status = reinterpret_cast<const int*>(w + q.w.status);
+        a.pcap = q.w.pcap;
+        a.pop = q.pop->pop;
+        a.X = q.data->X;
+        a.D = q.data->n_points;
+        a.F = q.data->n_features;
+        a.ldx = q.data->ldx;
+        a.y = q.y;
+        a.O = q.O;
+        a.out = q.out;
+        a.partial = reinterpret_cast<double*>(w + q.w.partial);
+        a.bt = sh.bt;
+        a.tp = sh.tp;
+        a.g = sh.g;
+        a.n_tiles = sh.n_tiles;
+        a.n_groups = sh.n_groups;
+        a.n_blocks = sh.n_blocks;
+        a.n_items = sh.n_items;
+        a.ctrl = reinterpret_cast<unsigned*>(w + q.w.ctrl);
+        total += sh.n_items;
+        b.end[m] = total;
+        if (sb > smem) smem = sb;
+        ++m;
+      }
+      if (m == 0) continue;
+      b.n = m;
+      const void* fn = find_eval_kernel(K, nw, modi, !mse);
+      if (!fn) return TGP_ERR_UNSUPPORTED;
+      if (smem > limit) return TGP_ERR_UNSUPPORTED;
+      if (!ensure_smem(fn, smem)) return TGP_ERR_CUDA;
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nw * 32, smem) != cudaSuccess)
+        return TGP_ERR_CUDA;
+      if (per_sm < 1) return TGP_ERR_UNSUPPORTED;
+      long long grid = (long long)dv.sms * per_sm;
+      if (grid > total) grid = total;
+      void* args[] = {&b};
+      if (cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(nw * 32), args, smem, st) != cudaSuccess)
+        return TGP_ERR_CUDA;
     }
-    if (m == 0) continue;
-    b.n = m;
-    const void* fn = find_eval_kernel(K, nw, modi, !mse);
-    if (!fn) return TGP_ERR_UNSUPPORTED;
-    if (smem > (size_t)dv.smem_optin) return TGP_ERR_UNSUPPORTED;
-    if (!ensure_smem(fn, smem)) return TGP_ERR_CUDA;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nw * 32, smem) != cudaSuccess)
-      return TGP_ERR_CUDA;
-    if (per_sm < 1) return TGP_ERR_UNSUPPORTED;
-    long long grid = (long long)dv.sms * per_sm;
-    if (grid > total) grid = total;
-    void* args[] = {&b};
-    if (cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(nw * 32), args, smem, st) != cudaSuccess)
-      return TGP_ERR_CUDA;
   }
   return TGP_OK;
 }
@@ -450,7 +473,7 @@ tgp_status run_backward(const tgp_population* pop, const tgp_data* data, const f
   Planned q{pop, data, y, O, nullptr, mse_out, tree_status};
   q.w = w;
   q.base = 0;
-  tgp_status s = launch_stage(&q, 1, wsb, st, dv);
+  tgp_status s = launch_stage(&q, 1, wsb, st, dv, true);
   if (s != TGP_OK) return s;
   const int K = 4, nw = 8;
   for (int variant = 0; variant < 2; ++variant) {

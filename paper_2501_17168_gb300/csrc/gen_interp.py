@@ -188,9 +188,13 @@ class Gen:
         self.e("ld.shared.v2.u32 {r_nx, r_ny}, [r_ptr+8];")
         self.e("add.u32 r_ptr, r_ptr, 8;")
         self.e("mov.b32 cv, r_iy;")
-        self.e("and.b32 r_op, r_ix, 255;")
         self.e("TS: .branchtargets " + ", ".join(f"C{k}" for k in range(OP_COUNT)) + ";")
-        self.e("brx.idx.uni r_op, TS;")
+        if self.modi:
+            self.e("and.b32 r_op, r_ix, 255;")
+            self.e("brx.idx.uni r_op, TS;")
+        else:
+            # programs for the plain kernel carry nothing above the opcode
+            self.e("brx.idx.uni r_ix, TS;")
 
         # ---- terminators and leaf loads
         self.e(f"C{OP_END_ROOT}:")

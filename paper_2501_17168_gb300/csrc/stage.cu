@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(STAGE_WARPS * 32) stage_kernel(const __grid_co
               last_ldv = var ? pc : -1;
             }
             ins.y = ns.leaf[n];
-            ins.x |= (uint32_t)n << 16;  // leaf node index (constant gradients)
+            if (a.want_nodes) ins.x |= (uint32_t)n << 16;  // leaf node index (constant gradients)
             prog[pc++] = ins;
             down = false;
           } else {
@@ -228,14 +228,14 @@ __global__ void __launch_bounds__(STAGE_WARPS * 32) stage_kernel(const __grid_co
           ins.x = (modi ? (var ? OP_BV_M : OP_BC_M) : (var ? OP_BV : OP_BC)) + f;
           ins.x |= modi ? o8 : 0;
           ins.y = ns.leaf[cb];
-          ins.x |= (uint32_t)cb << 16;
+          if (a.want_nodes) ins.x |= (uint32_t)cb << 16;
         } else if (la) {
           bool var = kind_of(ns.info[ca]) == 0;
           if (modi) ins.x = ((var ? OP_RV_M : OP_RC_M) + f) | o8;
           else if (f == F_ADD || f == F_MUL) ins.x = (var ? OP_BV : OP_BC) + f;
           else ins.x = (var ? OP_RV : OP_RC) + f;
           ins.y = ns.leaf[ca];
-          ins.x |= (uint32_t)ca << 16;
+          if (a.want_nodes) ins.x |= (uint32_t)ca << 16;
         } else {
           int d = ns.slot[q];
           if (d >= R) { deep = true; break; }

@@ -118,6 +118,9 @@ struct StageArgs {
   int* status;
   int* user_status;   // may be null
   unsigned* ctrl;
+  int want_nodes;      // record leaf node positions (bits 16-31; the adjoint routes
+                       // constant gradients with them); 0 leaves bits 8-31 of
+                       // plain instructions zero so the opcode needs no masking
 };
 
 struct EvalArgs {
@@ -212,7 +215,10 @@ __host__ __device__ inline int batch_find(const long long* end, int n, long long
 }
 
 // control word indices
-enum { CTRL_COUNTER = 0, CTRL_ANY_MODI = 1, CTRL_ERROR = 2, CTRL_COUNTER_MODI = 3, CTRL_WORDS = 64 };
+// (CTRL_COUNTER_GROUP + 2*g + variant: work counters of the evaluation
+// launches, one per occupancy group g and kernel variant)
+enum { CTRL_COUNTER = 0, CTRL_ANY_MODI = 1, CTRL_ERROR = 2, CTRL_COUNTER_MODI = 3,
+       CTRL_COUNTER_GROUP = 8, CTRL_WORDS = 64 };
 // bits of the error word
 enum { ERR_MBAR_TIMEOUT = 1 };
 
