@@ -165,9 +165,9 @@ size_t tgp_batch_workspace_size(const tgp_problem* probs, int32_t n);
 /* SR fitness of n independent problems of uneven sizes (populations, tree
  * lengths, point counts, feature counts) in one stage launch, one persistent
  * evaluation launch per occupancy group and one finalize launch.  Problems
- * whose shared-memory footprint allows the same number of CTAs per SM form a
- * group (at most three groups, doubled when single-output and Modi
- * populations are mixed); within a group the persistent CTAs pull work items
+ * whose shared-memory footprint allows the same number of resident CTAs per
+ * SM form a group (for each of the two kernel variants when single-output
+ * and Modi populations are mixed); within a group the persistent CTAs pull work items
  * of every problem from one counter, so small and large problems fill the
  * GPU together.  Same per-problem results as tgp_fitness_mse.  All problems
  * with one output must use the same points_per_lane.  Legal in

@@ -23,7 +23,10 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 constexpr int kNW = 8;
-constexpr int kCtasPerSm = 3;  // resident evaluation CTAs the shape heuristic aims for
+constexpr int kCtasPerSm = 3;     // resident evaluation CTAs the shape heuristic aims for
+constexpr int kMaxCtasPerSm = 8;  // 2048 threads per SM / 256 per CTA
+constexpr int kMaxGroups = TGP_MAX_PROBLEMS;  // evaluation launches per kernel variant in a batch
+static_assert(CTRL_COUNTER_GROUP + 2 * kMaxGroups <= CTRL_WORDS, "control block too small");
 
 struct DevInfo {
   bool init = false;
@@ -258,9 +261,19 @@ tgp_status launch_stage(Planned* qs, int n, char* ws, cudaStream_t st, const Dev
 // Launches the evaluation kernels over every problem's work items (the plain
 // variant only when some problem has a single output; each variant skips the
 // items of problems whose Modi flag does not match it).  Problems are grouped
-// by how many CTAs of their shared-memory footprint fit on an SM, and each
-// group gets one persistent launch sized for that occupancy, so a problem
-// with wide tiles does not lower the occupancy of the others.
+// by the number of CTAs of their shared-memory footprint that fit on an SM
+// and by the carve-out that occupancy needs, and each group gets one
+// persistent launch sized for it, so a problem with wide tiles lowers neither
+// the occupancy nor the L1 share of the others.
+// Index of the smallest shared-memory carve-out step (KB) of an SM that
+// holds `bytes`.
+int carveout_step(size_t bytes) {
+  static const int kSteps[] = {0, 8, 16, 32, 64, 100, 132, 164, 196, 228};
+  for (int i = 0; i < 10; ++i)
+    if (bytes <= (size_t)kSteps[i] * 1024) return i;
+  return 10;
+}
+
 tgp_status launch_eval(Planned* qs, int n, char* ws, unsigned* counters, cudaStream_t st,
                        const DevInfo& dv, bool mse) {
   bool any_single = false;
@@ -269,25 +282,45 @@ tgp_status launch_eval(Planned* qs, int n, char* ws, unsigned* counters, cudaStr
   for (int variant = 0; variant < 2; ++variant) {
     const bool modi = variant == 1;
     if (!modi && !any_single) continue;
-    for (int cls = kCtasPerSm; cls >= 1; --cls) {
-      const size_t lo = cls < kCtasPerSm ? limit / (cls + 1) - 1024 : 0;
-      const size_t hi = cls > 1 ? limit / cls - 1024 : limit;
+    int occ[TGP_MAX_PROBLEMS];
+    size_t sbytes[TGP_MAX_PROBLEMS];
+    int K = 0, nw = 0;
+    for (int i = 0; i < n; ++i) {
+      occ[i] = 0;
+      const Planned& q = qs[i];
+      if (q.pop->pop == 0 || q.data->n_points == 0) continue;
+      if (!modi && q.O > 1) continue;
+      const Shape& sh = modi ? q.sm : q.sp;
+      if (K && (sh.K != K || sh.nw != nw)) return TGP_ERR_UNSUPPORTED;
+      K = sh.K;
+      nw = sh.nw;
+      sbytes[i] = eval_smem_bytes(sh.K, sh.nw, modi, mse, sh.bt, q.w.pcap, sh.tp, q.data->n_features, q.O);
+      if (sbytes[i] > limit) return TGP_ERR_UNSUPPORTED;
+      const void* fn = find_eval_kernel(K, nw, modi, !mse);
+      if (!fn) return TGP_ERR_UNSUPPORTED;
+      if (!ensure_smem(fn, sbytes[i])) return TGP_ERR_CUDA;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[i], fn, nw * 32, sbytes[i]) != cudaSuccess)
+        return TGP_ERR_CUDA;
+      if (occ[i] < 1) return TGP_ERR_UNSUPPORTED;
+      if (occ[i] > kMaxCtasPerSm) occ[i] = kMaxCtasPerSm;
+      // group key: occupancy, then the L1/shared-memory split the SM needs
+      // for it (a larger shared-memory carve-out leaves less L1 for the
+      // others, so problems are not mixed across carve-out steps)
+      occ[i] = occ[i] * 16 + carveout_step((size_t)occ[i] * (sbytes[i] + 1024));
+    }
+    if (K == 0) continue;
+    const void* fn = find_eval_kernel(K, nw, modi, !mse);
+    int ngroup = 0;
+    for (int key = kMaxCtasPerSm * 16 + 15; key >= 16; --key) {
       EvalBatch b{};
-      b.counter = counters + CTRL_COUNTER_GROUP + 2 * (kCtasPerSm - cls) + (modi ? 1 : 0);
+      const int per_sm = key / 16;
       long long total = 0;
       size_t smem = 0;
-      int K = 0, nw = 0, m = 0;
+      int m = 0;
       for (int i = 0; i < n; ++i) {
+        if (occ[i] != key) continue;
         const Planned& q = qs[i];
-        if (q.pop->pop == 0 || q.data->n_points == 0) continue;
-        if (!modi && q.O > 1) continue;
         const Shape& sh = modi ? q.sm : q.sp;
-        const size_t sb =
-            eval_smem_bytes(sh.K, sh.nw, modi, mse, sh.bt, q.w.pcap, sh.tp, q.data->n_features, q.O);
-        if (!(sb > lo && sb <= hi)) continue;
-        if (m > 0 && (sh.K != K || sh.nw != nw)) return TGP_ERR_UNSUPPORTED;
-        K = sh.K;
-        nw = sh.nw;
         char* w = ws + q.base;
         EvalArgs& a = b.p[m];
         a.prog = reinterpret_cast<const uint2*>(w + q.w.prog);
@@ -313,19 +346,13 @@ tgp_status launch_eval(Planned* qs, int n, char* ws, unsigned* counters, cudaStr
         a.ctrl = reinterpret_cast<unsigned*>(w + q.w.ctrl);
         total += sh.n_items;
         b.end[m] = total;
-        if (sb > smem) smem = sb;
+        if (sbytes[i] > smem) smem = sbytes[i];
         ++m;
       }
       if (m == 0) continue;
+      if (ngroup >= kMaxGroups) return TGP_ERR_UNSUPPORTED;
+      b.counter = counters + CTRL_COUNTER_GROUP + 2 * ngroup++ + (modi ? 1 : 0);
       b.n = m;
-      const void* fn = find_eval_kernel(K, nw, modi, !mse);
-      if (!fn) return TGP_ERR_UNSUPPORTED;
-      if (smem > limit) return TGP_ERR_UNSUPPORTED;
-      if (!ensure_smem(fn, smem)) return TGP_ERR_CUDA;
-      int per_sm = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nw * 32, smem) != cudaSuccess)
-        return TGP_ERR_CUDA;
-      if (per_sm < 1) return TGP_ERR_UNSUPPORTED;
       long long grid = (long long)dv.sms * per_sm;
       if (grid > total) grid = total;
       void* args[] = {&b};

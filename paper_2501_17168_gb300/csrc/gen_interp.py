@@ -1,15 +1,34 @@
-"""Generates interp_fwd.cuh: the forward register-machine interpreter as one
-inline-PTX loop with a jump-table dispatch (brx.idx over .branchtargets).
+"""Generates the forward register-machine interpreter (interp_fwd.cuh) and
+its instruction-set header (isa_fwd.cuh).
 
-Why PTX: the instruction stream of a compiled tree is warp-uniform, so the
-ideal dispatch is one indirect branch per instruction.  A C++ `switch` over
-the 235 opcodes is lowered to a compare-and-branch tree and, with 72+
-loop-carried floats (the accumulator and eight slots of K points), to
-register shuffling at every case; a hand-written loop keeps every slot in a
-fixed register and dispatches with one brx.idx.
+The forward instruction set.  A compiled tree is a sequence of 64-bit words
+run by one warp over 32*K data points (K per lane).  The value of a subtree
+evaluated at nesting level d lives in register group G[d] (K floats per lane);
+level d is chosen by the stage compiler so that a binary node whose children
+are both subtrees evaluates the child that needs more levels first into G[d]
+and the other into G[d+1] (Sethi-Ullman order), then combines them into
+G[d].  Nothing is ever copied between groups, so evaluation order costs no
+moves.  Levels 0..NREG-1 are registers; deeper nesting (trees whose
+Sethi-Ullman number exceeds NREG) saves G[NREG-1] to a per-thread memory
+stack of MAXS entries and combines with it later.
+Leaves never get an instruction of their own: a leaf operand rides in its
+parent's word (feature index or constant bits), and a binary node with two
+leaf children is one instruction (two words when the operands need more than
+32 bits).  A Modi node (Sec. IV-C) adds its function value into its output
+accumulator and leaves its rightmost child's value in the group.
 
-Semantics per opcode are the ones listed in tgp_internal.cuh (enum Op).  The
-FP32 function bodies:
+Word layout: .x = opcode | out_index << 16 (Modi forms only), .y = operand.
+Opcodes are form_base + sub * NREG + d for the level forms (sub = function
+index) and form_base + sub for the memory-stack forms (push and pop through
+a stack-pointer register).
+
+Why PTX: the instruction stream is warp-uniform, so the ideal dispatch is
+one indirect branch per instruction; a C++ switch is lowered to a compare
+tree and shuffles the register groups at every case.  A hand-written loop
+keeps every group in fixed registers and dispatches with one brx.idx over a
+.branchtargets table.
+
+The FP32 function bodies:
   add/sub/mul   add.rn / sub.rn / mul.rn (never contracted)
   pdiv(a,b)     |b| > 1e-6f ? a * rcp.approx(b) : 1
   max           max.f32 (a NaN operand yields the other one)
@@ -20,6 +39,10 @@ FP32 function bodies:
   cexp(a)       ex2.approx.ftz(min(a, 80) * log2 e)
   tan(a)        sin.approx(r) * rcp.approx(cos.approx(r))
 
+The OP_* constants below are the accumulator-and-slots instruction set that
+the adjoint kernel runs (tgp_internal.cuh, enum Op); gen_interp_bwd.py
+imports them together with the function constants.
+
 Run `python gen_interp.py` to regenerate (the build does it when stale).
 """
 from __future__ import annotations
@@ -29,6 +52,7 @@ import struct
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(HERE, "interp_fwd.cuh")
+OUT_ISA = os.path.join(HERE, "isa_fwd.cuh")
 
 R = 8
 F_ADD, F_SUB, F_MUL, F_PDIV, F_MAX, F_SIN, F_COS, F_PLOG, F_CEXP, F_TAN = range(10)
@@ -59,44 +83,110 @@ C2 = fhex(1.9353072e-3)       # ... and the rest, rounded to float
 MAGIC = fhex(12582912.0)      # 1.5 * 2^23: x + MAGIC - MAGIC = rint(x) for |x| < 2^22
 
 
+# ------------------------------------------------------------------ forward ISA
+NREG = 3          # nesting levels held in registers
+MAXS = 6          # memory-stack entries: trees of <= 1024 nodes need <= 9 levels
+NC = [F_SUB, F_PDIV]   # non-commutative binary functions (max is symmetric in PTX)
+
+# (name, number of sub-forms); level forms come first, then memory forms
+LEVEL_FORMS = [
+    ("LDV", 1), ("LDC", 1),                       # G[d] = x[v] / c (only a lone leaf)
+    ("UN", 5), ("UNV", 5), ("UNC", 5),            # G[d] = f(G[d]) / f(x[v]) / f(c)
+    ("BV", 5), ("BC", 5),                         # G[d] = f(G[d], x[v]) / f(G[d], c)
+    ("RV", 2), ("RC", 2),                         # G[d] = f(x[v], G[d]) / f(c, G[d])
+    ("VV", 5),                                    # G[d] = f(x[v1], x[v2]), y = v1 | v2 << 16
+    ("VC", 5), ("CV", 2),                         # f(x[v], c) / f(c, x[v]); second word .x = v
+    ("CC", 5),                                    # f(c1, c2); second word .x = bits of c2
+    ("BS", 5), ("RS", 2),                         # G[d] = f(G[d], G[d+1]) / f(G[d+1], G[d])
+    ("UN_M", 5), ("UNV_M", 5), ("UNC_M", 5),      # Modi: out += f(.), G[d] = the operand
+    ("BV_M", 5), ("BC_M", 5), ("RV_M", 5), ("RC_M", 5),
+    ("BS_M", 5), ("RS_M", 5),
+]
+MEM_FORMS = [
+    ("SAVE", 1),                                  # push G[NREG-1]
+    ("MS", 5), ("SM", 2),                         # pop m: G = f(m, G) / f(G, m)  (G = G[NREG-1])
+    ("MS_M", 5), ("SM_M", 5),
+]
+
+
+def isa_layout():
+    base, op = {}, 2
+    for name, n in LEVEL_FORMS:
+        base[name] = op
+        op += n * NREG
+    for name, n in MEM_FORMS:
+        base[name] = op
+        op += n
+    return base, op
+
+
+FX_BASE, FX_COUNT = isa_layout()
+
+
+def fx(name, sub, lvl):
+    n = dict(LEVEL_FORMS + MEM_FORMS)[name]
+    assert 0 <= sub < n
+    if name in dict(MEM_FORMS):
+        assert lvl == 0
+        return FX_BASE[name] + sub
+    assert 0 <= lvl < NREG
+    return FX_BASE[name] + sub * NREG + lvl
+
+
 class Gen:
     def __init__(self, K: int, modi: bool):
         self.K = K
         self.modi = modi
         self.lines: list[str] = []
+        self.defined: set[int] = set()
 
     def e(self, s: str):
         self.lines.append(s)
 
-    # register names
-    def A(self, j):
-        return f"A{j}"
+    # ---- register names
+    @staticmethod
+    def G(d):
+        return lambda j: f"G{d}_{j}"
 
-    def S(self, d, j):
-        return f"S{d}_{j}"
-
-    def Lr(self, j):
-        return f"L{j}"
-
-    def T(self, j):
-        return f"T{j}"
-
-    def U(self, j):
-        return f"U{j}"
+    @staticmethod
+    def named(p):
+        return lambda j: f"{p}{j}"
 
     # ---- operand loads
-    def load_x(self, dst):
-        """dst[j] = X tile value of the lane's point j, feature = iy."""
-        K = self.K
-        self.e("mad.lo.u32 r_ad, r_iy, r_xstr, r_xc;")
+    def load_x(self, dst, idx):
+        """dst[j] = X tile value of the lane's point j, feature = register idx."""
+        self.e(f"mad.lo.u32 r_ad, {idx}, r_xstr, r_xc;")
         self.e(f"ld.shared.v4.f32 {{{dst(0)}, {dst(1)}, {dst(2)}, {dst(3)}}}, [r_ad];")
-        if K == 8:
+        if self.K == 8:
             self.e(f"ld.shared.v4.f32 {{{dst(4)}, {dst(5)}, {dst(6)}, {dst(7)}}}, [r_ad+512];")
+
+    def refetch(self):
+        """Skips the second word of a two-word instruction (already in r_nx)."""
+        self.e("ld.shared.v2.u32 {r_nx, r_ny}, [r_ptr+8];")
+        self.e("add.u32 r_ptr, r_ptr, 8;")
+
+    def movs(self, dst, src):
+        for j in range(self.K):
+            self.e(f"mov.f32 {dst(j)}, {src(j)};")
+
+    def mem_pop(self, dst):
+        """dst = top of the memory stack (r_sp = local address one past it)."""
+        K = self.K
+        self.e(f"sub.u32 r_sp, r_sp, {K * 4};")
+        for h in range(K // 4):
+            self.e(f"ld.local.v4.f32 {{{dst(4*h)}, {dst(4*h+1)}, {dst(4*h+2)}, {dst(4*h+3)}}}, "
+                   f"[r_sp+{16 * h}];")
+
+    def mem_push(self, src):
+        K = self.K
+        for h in range(K // 4):
+            self.e(f"st.local.v4.f32 [r_sp+{16 * h}], "
+                   f"{{{src(4*h)}, {src(4*h+1)}, {src(4*h+2)}, {src(4*h+3)}}};")
+        self.e(f"add.u32 r_sp, r_sp, {K * 4};")
 
     # ---- function bodies: out[j] = f(a[j], b[j]); a, b, out are name functions
     def fn2(self, f, out, a, b):
-        K = self.K
-        for j in range(K):
+        for j in range(self.K):
             o, x, y = out(j), a(j), b(j)
             if f == F_ADD:
                 self.e(f"add.rn.f32 {o}, {x}, {y};")
@@ -122,8 +212,7 @@ class Gen:
         self.e(f"fma.rn.f32 V{j}, W{j}, {C2}, V{j};")
 
     def fn1(self, f, out, a):
-        K = self.K
-        for j in range(K):
+        for j in range(self.K):
             o, x = out(j), a(j)
             if f == F_SIN:
                 self.reduce(j, x)
@@ -149,9 +238,9 @@ class Gen:
                 self.e(f"mul.rn.f32 {o}, V{j}, W{j};")
 
     def modi_add(self, src):
-        """out[o][lane points] += src[j] (o from bits 8..15 of ix)."""
+        """out[o][lane points] += src[j] (o from bits 16..23 of the word)."""
         K = self.K
-        self.e("bfe.u32 r_moo, r_ix, 8, 8;")
+        self.e("bfe.u32 r_moo, r_ix, 16, 8;")
         self.e(f"mad.lo.u32 r_ma, r_moo, {128 * K}, r_mo;")
         for h in range(K // 4):
             regs = [f"M{4 * h + q}" for q in range(4)]
@@ -161,22 +250,30 @@ class Gen:
                 self.e(f"add.rn.f32 {regs[q]}, {regs[q]}, {src(4 * h + q)};")
             self.e(f"st.shared.v4.f32 [r_ma{off}], {{{', '.join(regs)}}};")
 
-    def case(self, op, body):
+    def case(self, op, body, then=None):
+        """Label C<op>, its body, then back to the dispatch (or on to case `then`)."""
+        assert op not in self.defined
+        self.defined.add(op)
         self.e(f"C{op}:")
         body()
-        self.e("bra.uni LOOP;")
+        self.e(f"bra.uni C{then};" if then is not None else "bra.uni LOOP;")
 
     def build(self) -> str:
         K = self.K
-        A, Lr, T = self.A, self.Lr, self.T
-        c = lambda j: "cv"
+        G = self.G
+        L, T = self.named("L"), self.named("T")
+        cv = lambda j: "cv"
+        c2 = lambda j: "c2v"
+        top = NREG - 1
         self.e("{")
-        self.e(".reg .f32 " + ", ".join([f"A{j}" for j in range(K)] + [f"L{j}" for j in range(K)] +
-                                      [f"T{j}" for j in range(K)] + [f"V{j}" for j in range(K)] +
-                                      [f"W{j}" for j in range(K)] + [f"M{j}" for j in range(K)]) + ", cv;")
-        self.e(".reg .f32 " + ", ".join(self.S(d, j) for d in range(R) for j in range(K)) + ";")
+        temps = [f"{p}{j}" for p in "LTVWM" for j in range(K)]
+        self.e(".reg .f32 " + ", ".join(temps) + ", cv, c2v;")
+        self.e(".reg .f32 " + ", ".join(G(d)(j) for d in range(NREG) for j in range(K)) + ";")
         self.e(".reg .pred " + ", ".join(f"P{j}" for j in range(K)) + ";")
-        self.e(".reg .u32 r_ptr, r_ix, r_iy, r_nx, r_ny, r_op, r_ad, r_xc, r_xstr, r_mo, r_moo, r_ma, r_flag;")
+        self.e(".reg .u32 r_ptr, r_ix, r_iy, r_nx, r_ny, r_op, r_ad, r_xc, r_xstr, r_mo, r_moo, "
+               "r_ma, r_flag, r_t, r_sp;")
+        self.e(f".local .align 16 .b8 gm[{MAXS * K * 4}];")
+        self.e("mov.u32 r_sp, gm;")
         self.e("mov.u32 r_ptr, %{pg};")
         self.e("mov.u32 r_xc, %{xc};")
         self.e("mov.u32 r_xstr, %{xstr};")
@@ -188,124 +285,170 @@ class Gen:
         self.e("ld.shared.v2.u32 {r_nx, r_ny}, [r_ptr+8];")
         self.e("add.u32 r_ptr, r_ptr, 8;")
         self.e("mov.b32 cv, r_iy;")
-        self.e("TS: .branchtargets " + ", ".join(f"C{k}" for k in range(OP_COUNT)) + ";")
         if self.modi:
-            self.e("and.b32 r_op, r_ix, 255;")
+            self.e("and.b32 r_op, r_ix, 65535;")
             self.e("brx.idx.uni r_op, TS;")
         else:
-            # programs for the plain kernel carry nothing above the opcode
+            # plain programs carry nothing above the opcode
             self.e("brx.idx.uni r_ix, TS;")
 
-        # ---- terminators and leaf loads
-        self.e(f"C{OP_END_ROOT}:")
+        self.e("C0:")
         self.e("mov.u32 r_flag, 0;")
         self.e("bra.uni DONE;")
-        self.e(f"C{OP_END_MODI}:")
+        self.e("C1:")
         self.e("mov.u32 r_flag, 1;")
         self.e("bra.uni DONE;")
-        self.case(OP_LDV, lambda: self.load_x(A))
-        self.case(OP_LDC, lambda: [self.e(f"mov.f32 A{j}, cv;") for j in range(K)])
-        # ---- unary / fused unary-of-variable
-        for f in UNA:
-            self.case(OP_UN + f - F_SIN, lambda f=f: self.fn1(f, A, A))
-            self.case(OP_UNV + f - F_SIN, lambda f=f: (self.load_x(Lr), self.fn1(f, A, Lr)))
-        # ---- binary with a leaf operand
-        for f in BIN:
-            self.case(OP_BV + f, lambda f=f: (self.load_x(Lr), self.fn2(f, A, A, Lr)))
-            self.case(OP_BC + f, lambda f=f: self.fn2(f, A, A, c))
-            self.case(OP_RV + f, lambda f=f: (self.load_x(Lr), self.fn2(f, A, Lr, A)))
-            self.case(OP_RC + f, lambda f=f: self.fn2(f, A, c, A))
-        # ---- Modi forms (only reachable in the Modi kernel)
-        for f in UNA:
-            self.case(OP_UN_M + f - F_SIN,
-                      lambda f=f: (self.fn1(f, T, A), self.modi_add(T)) if self.modi else None)
-        for f in BIN:
-            def bvm(f=f):
-                if not self.modi:
-                    return
-                self.load_x(Lr)
-                self.fn2(f, T, A, Lr)
-                self.modi_add(T)
-                for j in range(K):
-                    self.e(f"mov.f32 A{j}, L{j};")
+        self.defined.update((0, 1))
 
-            def bcm(f=f):
-                if not self.modi:
-                    return
-                self.fn2(f, T, A, c)
-                self.modi_add(T)
-                for j in range(K):
-                    self.e(f"mov.f32 A{j}, cv;")
+        for d in range(NREG):
+            Gd = G(d)
+            self.case(fx("LDV", 0, d), lambda: self.load_x(Gd, "r_iy"))
+            self.case(fx("LDC", 0, d), lambda: self.movs(Gd, cv))
+            for u, f in enumerate(UNA):
+                un = fx("UN", u, d)
+                self.case(un, lambda f=f: self.fn1(f, Gd, Gd))
+                self.case(fx("UNV", u, d), lambda: self.load_x(Gd, "r_iy"), then=un)
+                self.case(fx("UNC", u, d), lambda: self.movs(Gd, cv), then=un)
+            # levels above d hold no live value while an instruction of level d
+            # runs, so below the top level a leaf operand is loaded into
+            # G[d+1] and the slot-combining body of BS/RS is reused
+            Gn = G(d + 1) if d < top else L
+            for f in BIN:
+                bv, bc = fx("BV", f, d), fx("BC", f, d)
+                if d < top:
+                    self.case(bv, lambda: self.load_x(Gn, "r_iy"), then=fx("BS", f, d))
+                else:
+                    self.case(bv, lambda f=f: (self.load_x(L, "r_iy"), self.fn2(f, Gd, Gd, L)))
+                self.case(bc, lambda f=f: self.fn2(f, Gd, Gd, cv))
 
-            def rvm(f=f):
-                if not self.modi:
-                    return
-                self.load_x(Lr)
-                self.fn2(f, T, Lr, A)
-                self.modi_add(T)
+                def vv():
+                    self.e("and.b32 r_t, r_iy, 65535;")
+                    self.load_x(Gd, "r_t")
+                    self.e("shr.u32 r_iy, r_iy, 16;")
+                    if d < top:
+                        self.load_x(Gn, "r_iy")
 
-            def rcm(f=f):
-                if not self.modi:
-                    return
-                self.fn2(f, T, c, A)
-                self.modi_add(T)
+                self.case(fx("VV", f, d), vv, then=fx("BS", f, d) if d < top else bv)
 
-            self.case(OP_BV_M + f, bvm)
-            self.case(OP_BC_M + f, bcm)
-            self.case(OP_RV_M + f, rvm)
-            self.case(OP_RC_M + f, rcm)
-        # ---- spill + leaf load
-        for d in range(R):
-            def spv(d=d):
-                for j in range(K):
-                    self.e(f"mov.f32 {self.S(d, j)}, A{j};")
-                self.load_x(A)
+                def vc():
+                    self.load_x(Gd, "r_nx")
+                    self.refetch()
 
-            def spc(d=d):
-                for j in range(K):
-                    self.e(f"mov.f32 {self.S(d, j)}, A{j};")
-                    self.e(f"mov.f32 A{j}, cv;")
+                self.case(fx("VC", f, d), vc, then=bc)
 
-            self.case(OP_SPV + d, spv)
-            self.case(OP_SPC + d, spc)
-        # ---- binary on a slot
-        for f in BIN:
-            for d in range(R):
-                Sd = lambda j, d=d: self.S(d, j)
-                self.case(OP_BS + f * R + d, lambda f=f, Sd=Sd: self.fn2(f, A, Sd, A))
-        for f in BIN:
-            for d in range(R):
-                Sd = lambda j, d=d: self.S(d, j)
-                self.case(OP_RS + f * R + d, lambda f=f, Sd=Sd: self.fn2(f, A, A, Sd))
-        for f in BIN:
-            for d in range(R):
-                Sd = lambda j, d=d: self.S(d, j)
+                def cc(f=f):
+                    self.e("mov.b32 c2v, r_nx;")
+                    self.refetch()
+                    self.fn2(f, Gd, cv, c2)
 
-                def bsm(f=f, Sd=Sd):
-                    if not self.modi:
-                        return
-                    self.fn2(f, T, Sd, A)
+                self.case(fx("CC", f, d), cc)
+                if d < top:
+                    self.case(fx("BS", f, d), lambda f=f: self.fn2(f, Gd, Gd, G(d + 1)))
+            for i, f in enumerate(NC):
+                rc = fx("RC", i, d)
+                if d < top:
+                    self.case(fx("RV", i, d), lambda: self.load_x(Gn, "r_iy"), then=fx("RS", i, d))
+                else:
+                    self.case(fx("RV", i, d), lambda f=f: (self.load_x(L, "r_iy"), self.fn2(f, Gd, L, Gd)))
+                self.case(rc, lambda f=f: self.fn2(f, Gd, cv, Gd))
+
+                def cvx():
+                    self.load_x(Gd, "r_nx")
+                    self.refetch()
+
+                self.case(fx("CV", i, d), cvx, then=rc)
+                if d < top:
+                    self.case(fx("RS", i, d), lambda f=f: self.fn2(f, Gd, G(d + 1), Gd))
+            if not self.modi:
+                continue
+            for u, f in enumerate(UNA):
+                unm = fx("UN_M", u, d)
+                self.case(unm, lambda f=f: (self.fn1(f, T, Gd), self.modi_add(T)))
+                self.case(fx("UNV_M", u, d), lambda: self.load_x(Gd, "r_iy"), then=unm)
+                self.case(fx("UNC_M", u, d), lambda: self.movs(Gd, cv), then=unm)
+            for f in BIN:
+                def bvm(f=f):
+                    self.load_x(L, "r_iy")
+                    self.fn2(f, T, Gd, L)
+                    self.modi_add(T)
+                    self.movs(Gd, L)
+
+                def bcm(f=f):
+                    self.fn2(f, T, Gd, cv)
+                    self.modi_add(T)
+                    self.movs(Gd, cv)
+
+                def rvm(f=f):
+                    self.load_x(L, "r_iy")
+                    self.fn2(f, T, L, Gd)
                     self.modi_add(T)
 
-                self.case(OP_BS_M + f * R + d, bsm)
-        for f in BIN:
-            for d in range(R):
-                Sd = lambda j, d=d: self.S(d, j)
-
-                def rsm(f=f, Sd=Sd, d=d):
-                    if not self.modi:
-                        return
-                    self.fn2(f, T, A, Sd)
+                def rcm(f=f):
+                    self.fn2(f, T, cv, Gd)
                     self.modi_add(T)
-                    for j in range(K):
-                        self.e(f"mov.f32 A{j}, {self.S(d, j)};")
 
-                self.case(OP_RS_M + f * R + d, rsm)
+                if d < top:
+                    # the leaf operand goes to G[d+1]; BS_M/RS_M do the rest
+                    self.case(fx("BV_M", f, d), lambda: self.load_x(Gn, "r_iy"), then=fx("BS_M", f, d))
+                    self.case(fx("BC_M", f, d), lambda: self.movs(Gn, cv), then=fx("BS_M", f, d))
+                    self.case(fx("RV_M", f, d), lambda: self.load_x(Gn, "r_iy"), then=fx("RS_M", f, d))
+                    self.case(fx("RC_M", f, d), lambda: self.movs(Gn, cv), then=fx("RS_M", f, d))
+                else:
+                    self.case(fx("BV_M", f, d), bvm)
+                    self.case(fx("BC_M", f, d), bcm)
+                    self.case(fx("RV_M", f, d), rvm)
+                    self.case(fx("RC_M", f, d), rcm)
+                if d < top:
+                    def bsm(f=f):
+                        self.fn2(f, T, Gd, G(d + 1))
+                        self.modi_add(T)
+                        self.movs(Gd, G(d + 1))
+
+                    def rsm(f=f):
+                        self.fn2(f, T, G(d + 1), Gd)
+                        self.modi_add(T)
+
+                    self.case(fx("BS_M", f, d), bsm)
+                    self.case(fx("RS_M", f, d), rsm)
+
+        Gt = G(top)
+        self.case(fx("SAVE", 0, 0), lambda: self.mem_push(Gt))
+        for f in BIN:
+            self.case(fx("MS", f, 0), lambda f=f: (self.mem_pop(L), self.fn2(f, Gt, L, Gt)))
+        for i, f in enumerate(NC):
+            self.case(fx("SM", i, 0), lambda f=f: (self.mem_pop(L), self.fn2(f, Gt, Gt, L)))
+        if self.modi:
+            for f in BIN:
+                def msm(f=f):
+                    self.mem_pop(L)
+                    self.fn2(f, T, L, Gt)
+                    self.modi_add(T)
+
+                def smm(f=f):
+                    self.mem_pop(L)
+                    self.fn2(f, T, Gt, L)
+                    self.modi_add(T)
+                    self.movs(Gt, L)
+
+                self.case(fx("MS_M", f, 0), msm)
+                self.case(fx("SM_M", f, 0), smm)
+
+        # opcodes the stage compiler never emits for this kernel: end with NaN
+        self.e("CBAD:")
+        for j in range(K):
+            self.e(f"mov.f32 G0_{j}, 0f7FC00000;")
+        self.e("mov.u32 r_flag, 0;")
+        self.e("bra.uni DONE;")
         self.e("DONE:")
         for j in range(K):
-            self.e(f"mov.f32 %{{a{j}}}, A{j};")
+            self.e(f"mov.f32 %{{a{j}}}, G0_{j};")
         self.e("mov.u32 %{flag}, r_flag;")
         self.e("}")
+        # the jump table goes right after the dispatch
+        table = "TS: .branchtargets " + ", ".join(
+            (f"C{k}" if k in self.defined else "CBAD") for k in range(FX_COUNT)) + ";"
+        i = self.lines.index("C0:")
+        self.lines.insert(i - 3 if self.modi else i - 2, table)
         return "\n".join(self.lines)
 
 
@@ -337,10 +480,42 @@ __device__ __forceinline__ unsigned interp_fwd<{K}, {'true' if modi else 'false'
 """
 
 
+def render_isa() -> str:
+    out = [
+        "// isa_fwd.cuh -- GENERATED by gen_interp.py; do not edit by hand.",
+        "// Opcodes of the forward instruction set run by interp_fwd (level registers",
+        "// G[0..NREG-1], a per-thread memory stack of MAXS entries).  A level form's",
+        "// opcode is base + sub * NREG + d, a memory form's base + sub; sub is the",
+        "// unary index f - F_SIN, the binary function f, or for the forms that exist",
+        "// only for non-commutative functions nc_index(f).  Word: .x = opcode |",
+        "// out_index << 16 (Modi forms), .y = operand; VC/CV/CC take a second word",
+        "// whose .x is the feature index (VC, CV) or the bits of the second constant",
+        "// (CC).",
+        "#pragma once",
+        "#include <cstdint>",
+        "namespace tgp {",
+        "namespace fx {",
+        f"constexpr int NREG = {NREG};",
+        f"constexpr int MAXS = {MAXS};",
+        "enum : uint32_t {",
+        "  END_ROOT = 0,  // output := G[0] (one output, no Modi node)",
+        "  END_MODI = 1,  // outputs are the Modi accumulators",
+    ]
+    for name, _ in LEVEL_FORMS + MEM_FORMS:
+        out.append(f"  {name} = {FX_BASE[name]},")
+    out.append(f"  COUNT = {FX_COUNT}")
+    out.append("};")
+    out.append("// index of a non-commutative binary function among the two-entry forms")
+    out.append("__host__ __device__ constexpr int nc_index(int f) { return f == 1 ? 0 : f == 3 ? 1 : -1; }")
+    out.append("}  // namespace fx")
+    out.append("}  // namespace tgp")
+    return "\n".join(out) + "\n"
+
+
 def main():
     parts = [
         "// interp_fwd.cuh -- GENERATED by gen_interp.py; do not edit by hand.",
-        "// Forward interpreter loop of the register machine (see tgp_internal.cuh).",
+        "// Forward interpreter loop of the level-register machine (isa_fwd.cuh).",
         "// interp_fwd<K, MODI>(pg, xc, xstr, mo, acc): pg = shared address of the",
         "// program, xc = shared address of the lane's first point of feature 0,",
         "// xstr = bytes between feature rows, mo = shared address of the lane's Modi",
@@ -356,6 +531,7 @@ def main():
         parts.append(render(K, modi))
     parts.append("}  // namespace tgp")
     open(OUT, "w").write("\n".join(parts) + "\n")
+    open(OUT_ISA, "w").write(render_isa())
     return OUT
 
 

@@ -12,6 +12,7 @@
 // numbering), and a stack-free walk over parent links emits the post-order
 // instruction stream with leaves fused into their parents.
 #include "tgp_internal.cuh"
+#include "isa_fwd.cuh"
 
 namespace tgp {
 
@@ -30,6 +31,239 @@ constexpr int STAGE_WARPS = 4;
 __device__ __forceinline__ bool is_int(float v) { return isfinite(v) && v == floorf(v); }
 
 __device__ __forceinline__ int kind_of(uint32_t in) { return (in >> 4) & 3; }
+
+// Emits the forward program of a validated tree in the level-register
+// instruction set (isa_fwd.cuh): the value of a subtree evaluated at level d
+// goes to register group G[d]; of a binary node's two subtrees the one that
+// needs more levels is evaluated first at the node's level, the other one
+// level deeper (at level NREG-1 the first result is saved to the memory
+// stack instead and the other subtree reuses the level).  Leaf operands ride
+// in their parent's instruction.  Returns the number of words, or -1 if the
+// program would exceed cap words or the memory stack (neither happens for
+// trees of up to 1024 nodes: every non-leaf subtree has a leaf without a
+// word of its own, and the Sethi-Ullman number stays below NREG + MAXS).
+__device__ int compile_fx(NodeSmem& ns, bool single_out, uint2* prog, int cap) {
+  using namespace fx;
+  int pc = 0, n = 0, sdepth = 0;
+  bool down = true;
+  auto put = [&](uint32_t x, uint32_t y) {
+    if (pc >= cap) return false;
+    prog[pc++] = make_uint2(x, y);
+    return true;
+  };
+  ns.slot[0] = 0;
+  for (;;) {
+    const uint32_t in = ns.info[n];
+    const int k = kind_of(in);
+    if (down) {
+      const int lv = ns.slot[n];
+      if (k <= 1) {  // a lone leaf: the root, or the first operand of a Modi node
+        if (!put((k == 0 ? LDV : LDC) + lv, ns.leaf[n])) return -1;
+        down = false;
+        continue;
+      }
+      const bool modi = in & 64;
+      const int f = in & 15;
+      const uint32_t o16 = modi ? ((in >> 8) & 255) << 16 : 0;
+      if (k == 2) {
+        const int c = n + 1, ck = kind_of(ns.info[c]);
+        if (ck <= 1) {  // unary of a leaf: one instruction
+          const uint32_t base = modi ? (ck == 0 ? UNV_M : UNC_M) : (ck == 0 ? UNV : UNC);
+          if (!put((base + (f - F_SIN) * NREG + lv) | o16, ns.leaf[c])) return -1;
+          down = false;
+          continue;
+        }
+        ns.slot[c] = lv;
+        n = c;
+        continue;
+      }
+      const int ca = n + 1, cb = ca + ns.sz[ca];
+      const int ka = kind_of(ns.info[ca]), kb = kind_of(ns.info[cb]);
+      if (ka <= 1 && kb <= 1 && !modi) {  // two leaves: one instruction
+        const uint32_t la = ns.leaf[ca], lb = ns.leaf[cb];
+        const int nc = nc_index(f);
+        bool ok;
+        if (ka == 0 && kb == 0) ok = put(VV + f * NREG + lv, la | (lb << 16));
+        else if (ka == 0) ok = put(VC + f * NREG + lv, lb) && put(la, 0);
+        else if (kb == 0 && nc < 0) ok = put(VC + f * NREG + lv, la) && put(lb, 0);
+        else if (kb == 0) ok = put(CV + nc * NREG + lv, la) && put(lb, 0);
+        else ok = put(CC + f * NREG + lv, la) && put(lb, 0);
+        if (!ok) return -1;
+        down = false;
+        continue;
+      }
+      const int first = kb <= 1 ? ca : ka <= 1 ? cb : (ns.need[ca] >= ns.need[cb] ? ca : cb);
+      ns.slot[first] = lv;
+      n = first;
+      continue;
+    }
+    // ---- n is done: continue with its parent
+    if (n == 0) break;
+    const int q = ns.par[n];
+    const uint32_t qin = ns.info[q];
+    const int qk = kind_of(qin), f = qin & 15, lv = ns.slot[q];
+    const bool modi = qin & 64;
+    const uint32_t o16 = modi ? ((qin >> 8) & 255) << 16 : 0;
+    uint32_t x, y = 0;
+    if (qk == 2) {
+      x = (modi ? UN_M : UN) + (f - F_SIN) * NREG + lv;
+    } else {
+      const int ca = q + 1, cb = ca + ns.sz[ca];
+      const int ka = kind_of(ns.info[ca]), kb = kind_of(ns.info[cb]);
+      const int nc = nc_index(f);
+      if (kb <= 1) {  // b is a leaf, a is in G[lv]
+        x = (modi ? (kb == 0 ? BV_M : BC_M) : (kb == 0 ? BV : BC)) + f * NREG + lv;
+        y = ns.leaf[cb];
+      } else if (ka <= 1) {  // a is a leaf, b is in G[lv]
+        if (modi) x = (ka == 0 ? RV_M : RC_M) + f * NREG + lv;
+        else if (nc < 0) x = (ka == 0 ? BV : BC) + f * NREG + lv;
+        else x = (ka == 0 ? RV : RC) + nc * NREG + lv;
+        y = ns.leaf[ca];
+      } else {
+        const bool a_first = ns.need[ca] >= ns.need[cb];
+        const int first = a_first ? ca : cb, second = a_first ? cb : ca;
+        const bool mem = lv + 1 >= NREG;
+        if (n == first) {  // first operand done: evaluate the second one
+          if (mem) {
+            if (sdepth >= MAXS || !put(SAVE, 0)) return -1;
+            ++sdepth;
+            ns.slot[second] = lv;
+          } else {
+            ns.slot[second] = lv + 1;
+          }
+          n = second;
+          down = true;
+          continue;
+        }
+        if (!mem) {  // first operand in G[lv], second in G[lv+1]
+          if (a_first) x = (modi ? BS_M : BS) + f * NREG + lv;
+          else if (modi) x = RS_M + f * NREG + lv;
+          else if (nc < 0) x = BS + f * NREG + lv;
+          else x = RS + nc * NREG + lv;
+        } else {  // first operand on the memory stack, second in G[NREG-1]
+          --sdepth;
+          if (a_first) x = (modi ? MS_M : MS) + f;
+          else if (modi) x = SM_M + f;
+          else if (nc < 0) x = MS + f;
+          else x = SM + nc;
+        }
+      }
+    }
+    if (!put(x | o16, y)) return -1;
+    n = q;
+  }
+  if (!put(single_out ? END_ROOT : END_MODI, 0)) return -1;
+  return pc;
+}
+
+// Emits the adjoint program of a validated tree in the accumulator-and-slots
+// instruction set (enum Op): a post-order walk over parent links with leaves
+// fused into their parents; every leaf operand records its node position in
+// bits 16-31 (the adjoint routes constant gradients with it).  Returns the
+// number of words, or -1 when the tree needs more than R slots.
+__device__ int compile_adj(NodeSmem& ns, bool single_out, uint2* prog) {
+  int pc = 0;
+  int n = 0, pend = -1, last_ldv = -1;
+  bool down = true, deep = false;
+  ns.slot[0] = 0;
+  for (;;) {
+    uint32_t in = ns.info[n];
+    int k = kind_of(in);
+    if (down) {
+      int c = -1;
+      if (k == 2) {
+        c = n + 1;
+      } else if (k == 3) {
+        int ca = n + 1, cb = ca + ns.sz[ca];
+        bool la = kind_of(ns.info[ca]) <= 1, lb = kind_of(ns.info[cb]) <= 1;
+        c = lb ? ca : la ? cb : (ns.need[ca] >= ns.need[cb] ? ca : cb);
+      }
+      if (c < 0) {  // a leaf evaluated on its own: load it (spilling acc first if pending)
+        uint2 ins;
+        bool var = k == 0;
+        if (pend >= 0) {
+          ins.x = (var ? OP_SPV : OP_SPC) + pend;
+          pend = -1;
+          last_ldv = -1;
+        } else {
+          ins.x = var ? OP_LDV : OP_LDC;
+          last_ldv = var ? pc : -1;
+        }
+        ins.y = ns.leaf[n];
+        ins.x |= (uint32_t)n << 16;  // leaf node index (constant gradients)
+        prog[pc++] = ins;
+        down = false;
+      } else {
+        ns.slot[c] = ns.slot[n];
+        n = c;
+      }
+      continue;
+    }
+    if (n == 0) break;
+    int q = ns.par[n];
+    uint32_t qin = ns.info[q];
+    int qk = kind_of(qin);
+    int ca = q + 1, cb = ca + ns.sz[ca];
+    bool la = false, lb = false, a_first = true;
+    if (qk == 3) {
+      la = kind_of(ns.info[ca]) <= 1;
+      lb = kind_of(ns.info[cb]) <= 1;
+      a_first = ns.need[ca] >= ns.need[cb];
+      if (!la && !lb) {
+        int second = a_first ? cb : ca;
+        if (n != second) {  // first child done: spill it, evaluate the other one
+          pend = ns.slot[q];
+          if (pend >= R) { deep = true; break; }
+          ns.slot[second] = ns.slot[q] + 1;
+          n = second;
+          down = true;
+          continue;
+        }
+      }
+    }
+    // ---- emit the instruction of node q
+    int f = qin & 15;
+    bool modi = qin & 64;
+    uint32_t o8 = ((qin >> 8) & 255) << 8;
+    uint2 ins;
+    ins.y = 0;
+    if (qk == 2) {
+      if (modi) {
+        ins.x = (OP_UN_M + (f - F_SIN)) | o8;
+      } else if (last_ldv == pc - 1 && last_ldv >= 0) {
+        ins.x = OP_UNV + (f - F_SIN);  // fuse with the variable load just emitted
+        ins.y = prog[pc - 1].y;
+        --pc;
+      } else {
+        ins.x = OP_UN + (f - F_SIN);
+      }
+    } else if (lb) {
+      bool var = kind_of(ns.info[cb]) == 0;
+      ins.x = (modi ? (var ? OP_BV_M : OP_BC_M) : (var ? OP_BV : OP_BC)) + f;
+      ins.x |= modi ? o8 : 0;
+      ins.y = ns.leaf[cb];
+      ins.x |= (uint32_t)cb << 16;
+    } else if (la) {
+      bool var = kind_of(ns.info[ca]) == 0;
+      if (modi) ins.x = ((var ? OP_RV_M : OP_RC_M) + f) | o8;
+      else if (f == F_ADD || f == F_MUL) ins.x = (var ? OP_BV : OP_BC) + f;
+      else ins.x = (var ? OP_RV : OP_RC) + f;
+      ins.y = ns.leaf[ca];
+      ins.x |= (uint32_t)ca << 16;
+    } else {
+      int d = ns.slot[q];
+      if (d >= R) { deep = true; break; }
+      uint32_t base = a_first ? (modi ? OP_BS_M : OP_BS) : (modi ? OP_RS_M : OP_RS);
+      ins.x = (base + f * R + d) | (modi ? o8 : 0);
+    }
+    prog[pc++] = ins;
+    last_ldv = -1;
+    n = q;
+  }
+  if (deep) return -1;
+  prog[pc++] = make_uint2(single_out ? OP_END_ROOT : OP_END_MODI, 0u);
+  return pc;
+}
 
 __global__ void __launch_bounds__(STAGE_WARPS * 32) stage_kernel(const __grid_constant__ StageBatch b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -147,113 +381,15 @@ __global__ void __launch_bounds__(STAGE_WARPS * 32) stage_kernel(const __grid_co
         }
         ns.need[i] = (uint8_t)min(nd, 255);
       }
-      // ---- post-order walk over parent links, leaves fused into parents
       uint2* prog = a.prog + p * a.pcap;
-      int n = 0, pend = -1, last_ldv = -1;
-      bool down = true, deep = false;
-      ns.slot[0] = 0;
-      for (;;) {
-        uint32_t in = ns.info[n];
-        int k = kind_of(in);
-        if (down) {
-          int c = -1;
-          if (k == 2) {
-            c = n + 1;
-          } else if (k == 3) {
-            int ca = n + 1, cb = ca + ns.sz[ca];
-            bool la = kind_of(ns.info[ca]) <= 1, lb = kind_of(ns.info[cb]) <= 1;
-            c = lb ? ca : la ? cb : (ns.need[ca] >= ns.need[cb] ? ca : cb);
-          }
-          if (c < 0) {  // a leaf evaluated on its own: load it (spilling acc first if pending)
-            uint2 ins;
-            bool var = k == 0;
-            if (pend >= 0) {
-              ins.x = (var ? OP_SPV : OP_SPC) + pend;
-              pend = -1;
-              last_ldv = -1;
-            } else {
-              ins.x = var ? OP_LDV : OP_LDC;
-              last_ldv = var ? pc : -1;
-            }
-            ins.y = ns.leaf[n];
-            if (a.want_nodes) ins.x |= (uint32_t)n << 16;  // leaf node index (constant gradients)
-            prog[pc++] = ins;
-            down = false;
-          } else {
-            ns.slot[c] = ns.slot[n];
-            n = c;
-          }
-          continue;
-        }
-        if (n == 0) break;
-        int q = ns.par[n];
-        uint32_t qin = ns.info[q];
-        int qk = kind_of(qin);
-        int ca = q + 1, cb = ca + ns.sz[ca];
-        bool la = false, lb = false, a_first = true;
-        if (qk == 3) {
-          la = kind_of(ns.info[ca]) <= 1;
-          lb = kind_of(ns.info[cb]) <= 1;
-          a_first = ns.need[ca] >= ns.need[cb];
-          if (!la && !lb) {
-            int second = a_first ? cb : ca;
-            if (n != second) {  // first child done: spill it, evaluate the other one
-              pend = ns.slot[q];
-              if (pend >= R) { deep = true; break; }
-              ns.slot[second] = ns.slot[q] + 1;
-              n = second;
-              down = true;
-              continue;
-            }
-          }
-        }
-        // ---- emit the instruction of node q
-        int f = qin & 15;
-        bool modi = qin & 64;
-        uint32_t o8 = ((qin >> 8) & 255) << 8;
-        uint2 ins;
-        ins.y = 0;
-        if (qk == 2) {
-          if (modi) {
-            ins.x = (OP_UN_M + (f - F_SIN)) | o8;
-          } else if (last_ldv == pc - 1 && last_ldv >= 0) {
-            ins.x = OP_UNV + (f - F_SIN);  // fuse with the variable load just emitted
-            ins.y = prog[pc - 1].y;
-            --pc;
-          } else {
-            ins.x = OP_UN + (f - F_SIN);
-          }
-        } else if (lb) {
-          bool var = kind_of(ns.info[cb]) == 0;
-          ins.x = (modi ? (var ? OP_BV_M : OP_BC_M) : (var ? OP_BV : OP_BC)) + f;
-          ins.x |= modi ? o8 : 0;
-          ins.y = ns.leaf[cb];
-          if (a.want_nodes) ins.x |= (uint32_t)cb << 16;
-        } else if (la) {
-          bool var = kind_of(ns.info[ca]) == 0;
-          if (modi) ins.x = ((var ? OP_RV_M : OP_RC_M) + f) | o8;
-          else if (f == F_ADD || f == F_MUL) ins.x = (var ? OP_BV : OP_BC) + f;
-          else ins.x = (var ? OP_RV : OP_RC) + f;
-          ins.y = ns.leaf[ca];
-          if (a.want_nodes) ins.x |= (uint32_t)ca << 16;
-        } else {
-          int d = ns.slot[q];
-          if (d >= R) { deep = true; break; }
-          uint32_t base = a_first ? (modi ? OP_BS_M : OP_BS) : (modi ? OP_RS_M : OP_RS);
-          ins.x = (base + f * R + d) | (modi ? o8 : 0);
-        }
-        prog[pc++] = ins;
-        last_ldv = -1;
-        n = q;
+      if (!a.want_nodes) {
+        pc = compile_fx(ns, a.n_outputs == 1 && !modi_here, prog, a.pcap);
+      } else {
+        pc = compile_adj(ns, a.n_outputs == 1 && !modi_here, prog);
       }
-      if (deep) {
+      if (pc < 0) {
         st = S_DEPTH;
         pc = 0;
-      } else {
-        uint2 end;
-        end.x = (a.n_outputs == 1 && !modi_here) ? OP_END_ROOT : OP_END_MODI;
-        end.y = 0;
-        prog[pc++] = end;
       }
     }
     st = __shfl_sync(0xffffffffu, st, 0);

@@ -1,24 +1,28 @@
 // tgp_internal.cuh -- shared definitions of the sm_103a kernels: the compiled
-// instruction set, the FP32 function table, workspace layout and kernel
-// argument blocks.
+// instruction sets, workspace layout and kernel argument blocks.
 //
 // Evaluation model.  The paper evaluates a prefix tree with a value stack,
 // walking the nodes from the end to the start (Sec. III-C).  Here each tree is
 // first compiled (stage kernel) into a register-machine program for a warp:
 //   * one warp evaluates one tree over 32*K data points (K points per lane);
 //     every lane runs the same instruction, so dispatch never diverges;
-//   * the top of the stack is held in registers ("acc", K values per lane),
-//     the rest in R = 8 register slots s[0..7] addressed only by instruction
-//     variants with a compile-time slot number, so nothing spills to memory;
 //   * operands are evaluated in Sethi-Ullman order (the child that needs more
-//     slots first), which bounds the slots by log2(leaves) + 1: eight slots
+//     registers first), which bounds the registers by log2(leaves) + 1: nine
 //     cover every binary/unary tree of up to 1023 nodes;
 //   * leaves are fused into their parent's instruction (a variable operand is
 //     read from the shared-memory tile of X, a constant rides in the
 //     instruction word), so leaves cost no dispatch of their own;
 //   * a Modi node (Sec. IV-C) is one instruction that adds its function value
-//     into its output accumulator and leaves its rightmost child's value in
-//     acc for the parent.
+//     into its output accumulator and hands its parent its rightmost child's
+//     value.
+// Two instruction sets share this scheme.  The forward kernels run the
+// level-register set of isa_fwd.cuh (generated with its interpreter by
+// gen_interp.py): the value of a subtree at nesting level d lives in register
+// group G[d], so evaluation order costs no copies, and a binary node with two
+// leaf children is one instruction.  The adjoint runs the accumulator-and-
+// slots set below (enum Op): the top of the stack in "acc", the rest in R = 8
+// slots, and every leaf operand carries its node position for the constant
+// gradients.
 // Reordering the operand evaluation does not change any value: every
 // function is pure, only the order in which Modi contributions are summed
 // into an output changes.
@@ -40,7 +44,7 @@ constexpr int MAX_LEN = 1024;   // longest supported tree
 constexpr int MAX_OUT = 16;     // outputs
 constexpr int MAX_FEAT = 256;   // features
 
-// ------------------------------------------------------------- instruction set
+// ------------------------------------------------------------- adjoint instruction set
 // One instruction is a uint2: .x = opcode | out_index << 8 | leaf_node << 16;
 // .y = the leaf operand (feature index for *V forms, float bits of the
 // constant for *C forms).  leaf_node is the prefix position of the leaf
@@ -118,9 +122,8 @@ struct StageArgs {
   int* status;
   int* user_status;   // may be null
   unsigned* ctrl;
-  int want_nodes;      // record leaf node positions (bits 16-31; the adjoint routes
-                       // constant gradients with them); 0 leaves bits 8-31 of
-                       // plain instructions zero so the opcode needs no masking
+  int want_nodes;      // 1: adjoint programs (enum Op, leaf node positions in bits
+                       // 16-31); 0: forward programs (isa_fwd.cuh)
 };
 
 struct EvalArgs {
@@ -216,7 +219,7 @@ __host__ __device__ inline int batch_find(const long long* end, int n, long long
 
 // control word indices
 // (CTRL_COUNTER_GROUP + 2*g + variant: work counters of the evaluation
-// launches, one per occupancy group g and kernel variant)
+// launches, one per launch group g and kernel variant)
 enum { CTRL_COUNTER = 0, CTRL_ANY_MODI = 1, CTRL_ERROR = 2, CTRL_COUNTER_MODI = 3,
        CTRL_COUNTER_GROUP = 8, CTRL_WORDS = 64 };
 // bits of the error word
