@@ -59,6 +59,10 @@ def _args():
     ap.add_argument("--points", type=int, default=100_000, help="data points")
     ap.add_argument("--suite", action="store_true",
                     help="also time the other workloads (one JSON line each, after the main line)")
+    ap.add_argument("--case", default=None, choices=["adjoint", "modi", "batched"],
+                    help="time only one case for profiling: the fused forward + adjoint on the "
+                         "differentiation workload or the Modi forward (--pop/--points), or the "
+                         "8-problem uneven batch (one batched call, then one call per problem)")
     return ap.parse_args()
 
 
@@ -131,7 +135,7 @@ class ClockSampler:
 # ----------------------------------------------------------------- helpers
 def _src_hash():
     h = hashlib.sha256()
-    for f in ("eval.cu", "tgp_internal.cuh", "interp_fwd.cuh"):
+    for f in ("eval.cu", "stage.cu", "tgp_internal.cuh", "interp_fwd.cuh", "isa_fwd.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2501_17168_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -544,8 +548,56 @@ def suite_lines(dev, steps):
     return out
 
 
+def run_case(a):
+    """One small case for the kernel profiles: the fused forward + adjoint of
+    the differentiation workload (constants and inputs), or the Modi forward
+    (8 outputs), on --pop trees x --points points; prints one JSON line."""
+    import torch
+    from paper_2501_17168_gb300 import api, build, workloads as W
+    build.build_all()
+    dev = torch.device("cuda", 0)
+    if a.case == "batched":
+        bps = []
+        for pr in W.batched_uneven(0):
+            tt, vv, ss = api.population_to(pr.pop, dev)
+            Xp, yp = _gpu_targets(api, pr, dev)
+            bps.append(api.BatchProblem(tt, vv, ss, Xp, yp, 1, max_len=pr.pop.max_len))
+
+        def per_problem():
+            for bp in bps:
+                tt, vv, ss, Xp, yp = bp.tensors
+                api.tgp_fitness_mse(tt, vv, ss, Xp, yp, 1, max_len=bp.pop.max_len, mse=bp.mse,
+                                    tree_status=bp.status)
+        ms_b = _timed(lambda: api.tgp_batch_fitness_mse(bps), a.steps, a.warmup)
+        ms_p = _timed(per_problem, a.steps, a.warmup)
+        api.tgp_check_device_error(dev)
+        print(json.dumps({"case": "batched", "ms_batched": ms_b, "ms_one_launch_per_problem": ms_p}),
+              flush=True)
+        return 0
+    if a.case == "adjoint":
+        prob, O = W.diff(0, pop=a.pop, D=a.points), 1
+    else:
+        prob, O = W.modi(0, pop=a.pop, D=a.points), 8
+    t, v, s = api.population_to(prob.pop, dev)
+    X = torch.from_numpy(prob.X).to(dev)
+    y = torch.from_numpy(np.random.default_rng(0).standard_normal((prob.D, O)).astype(np.float32)).to(dev)
+    g = torch.full((prob.pop.pop, O), 1.0 / prob.pop.pop, dtype=torch.float64, device=dev)
+    if a.case == "adjoint":
+        fn = lambda: api.tgp_eval_backward(t, v, s, X, y, g, O, max_len=prob.pop.max_len)
+    else:
+        fn = lambda: api.tgp_fitness_mse(t, v, s, X, y, O, max_len=prob.pop.max_len)
+    ms = _timed(fn, a.steps, a.warmup)
+    api.tgp_check_device_error(dev)
+    print(json.dumps({"case": a.case, "pop": prob.pop.pop, "n_points": prob.D, "n_outputs": O,
+                      "ms_per_call": ms, "node_points_per_s": prob.pop.nodes() * prob.D / (ms / 1e3)}),
+          flush=True)
+    return 0
+
+
 def main():
     a = _args()
+    if a.case:
+        return run_case(a)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

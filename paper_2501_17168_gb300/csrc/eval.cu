@@ -137,11 +137,22 @@ __global__ void __launch_bounds__(NW * 32, 3) eval_kernel(const __grid_constant_
   unsigned char* smem = smem_all + 64;
   const long long total = b.end[b.n - 1];
 
+  // Return at once when this variant serves no problem of the batch (a
+  // single-output population without a Modi node skips the Modi kernel and
+  // vice versa), so the unused variant costs one short launch.
   if (tid == 0) {
+    int served = 0;
+    for (int i = 0; i < b.n; ++i) {
+      const EvalArgs& q = b.p[i];
+      served |= q.O > 1 ? (int)MODI
+                        : (int)((*((volatile unsigned*)&q.ctrl[CTRL_ANY_MODI]) != 0) == MODI);
+    }
+    *s_sub = served;
     mbar_init(mbar, 1);
     fence_mbar_init();
   }
   __syncthreads();
+  if (*s_sub == 0) return;
   uint32_t phase = 0;
 
   for (;;) {
