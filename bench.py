@@ -220,8 +220,9 @@ def cpu_baseline(prob, seconds_target=15.0):
     cores = os.cpu_count() or 1
     gt, _ = oracle.evaluate(prob.gt.type, prob.gt.val, prob.gt.size, prob.X, threads=cores)
     y = (gt[0, 0] + prob.noise[:, 0]).astype(np.float32)
-    # calibrate on a small slice, then time a sample of about seconds_target
-    pick = np.arange(0, prob.pop.pop, 500)
+    # calibrate on a slice with a few trees per core, then time a sample of
+    # about seconds_target
+    pick = np.arange(0, prob.pop.pop, max(1, prob.pop.pop // (4 * cores)))
     sub = prob.pop.take(pick)
     t0 = time.perf_counter()
     oracle.mse(sub.type, sub.val, sub.size, prob.X, y, threads=cores)
