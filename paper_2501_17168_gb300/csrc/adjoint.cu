@@ -118,9 +118,12 @@ __global__ void __launch_bounds__(NW * 32, 3) adjoint_kernel(AdjArgs a) {
       const long long p = (t + stagger) % a.pop;
       const int plen = a.plen[p];
       if (plen <= 0) continue;
-      bool active = a.want_mse;
-      for (int o = 0; o < O; ++o) active |= a.g[p * O + o] != 0.0;
-      if (!active) continue;
+      // a tree with zero upstream gradient only needs the forward (for its
+      // MSE); its reverse sweep is skipped, so that 0 * inf seeds of points
+      // where it overflows cannot put NaN into the shared X gradient
+      bool any_g = false;
+      for (int o = 0; o < O; ++o) any_g |= a.g[p * O + o] != 0.0;
+      if (!any_g && !a.want_mse) continue;
       // stage the program, clear the constant-gradient row, 2g/D per output
       for (int i = lane; i < plen; i += 32) prog_w[i] = a.prog[p * a.pcap + i];
       for (int i = lane; i < a.max_len; i += 32) cg_w[i] = 0.0f;
@@ -172,10 +175,11 @@ __global__ void __launch_bounds__(NW * 32, 3) adjoint_kernel(AdjArgs a) {
           }
         }
         __syncwarp();
-        bwd_reverse<K, MODI>(sm_addr(prog_w + (plen - 1)), sm_addr(prog_w), sm_addr(xs + qb),
-                             (unsigned)XS * 4u, sm_addr(gxs + ch * CH + lane), sm_addr(cg_w),
-                             sm_addr(sd_w + 4 * lane), tend, (unsigned)lane, sm_addr(slot_w + 4 * lane),
-                             seed);
+        if (any_g)
+          bwd_reverse<K, MODI>(sm_addr(prog_w + (plen - 1)), sm_addr(prog_w), sm_addr(xs + qb),
+                               (unsigned)XS * 4u, sm_addr(gxs + ch * CH + lane), sm_addr(cg_w),
+                               sm_addr(sd_w + 4 * lane), tend, (unsigned)lane,
+                               sm_addr(slot_w + 4 * lane), seed);
         __syncwarp();
       }
       // flush the tree's constant gradients and squared residuals

@@ -208,3 +208,22 @@ def test_adam_on_constants_reduces_the_loss():
     fin = torch.isfinite(first) & torch.isfinite(last) & mask.any(1, keepdim=True)
     improved = (last[fin] < first[fin]).float().mean().item()
     assert improved > 0.8, improved
+
+
+def test_zero_upstream_tree_that_overflows_leaves_grad_X_finite(orc):
+    # the fused MSE needs the forward of every tree, but a tree with zero
+    # upstream gradient must contribute nothing to the X gradient even where
+    # its value overflows (0 * inf would be NaN)
+    over = W.encode(["cexp", "cexp", "mul", ("c", 3.0), ("x", 0)])      # exp(exp(3 x0)) -> inf
+    tame = W.encode(["add", "mul", ("x", 0), ("c", 0.5), "sin", ("x", 1)])
+    p = W.stack([over, tame])
+    X = np.random.default_rng(19).uniform(-3, 3, (777, 2)).astype(np.float32)
+    y = np.zeros((777, 1), np.float32)
+    g = np.array([[0.0], [1.0]])
+    mse, gv, gx, st = gpu_backward(p, X, y, g)
+    assert np.isinf(mse[0, 0]) or mse[0, 0] > 1e30
+    rm, rgv, rgx, rst = orc.grad(p.type, p.val, p.size, X, y, g, max_len=p.max_len)
+    assert np.isfinite(gx).all()
+    np.testing.assert_allclose(gx, rgx, rtol=1e-3, atol=1e-3)
+    np.testing.assert_allclose(gv[1], rgv[1], rtol=1e-3, atol=1e-3)
+    assert (gv[0] == 0).all()
