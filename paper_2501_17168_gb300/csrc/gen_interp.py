@@ -133,12 +133,32 @@ def fx(name, sub, lvl):
     return FX_BASE[name] + sub * NREG + lvl
 
 
+def layout_key(op):
+    """Position of a case in the generated code.  The interpreter is bound
+    by instruction fetch, and the order of the cases in the code matters:
+    level-major order (all forms of level 0, then level 1, ...; within a
+    level the forms in LEVEL_FORMS order, then the function) with the
+    rarely used tan forms moved to the end measured fastest among the
+    orders tried (generation order, form-major, hot-forms-first,
+    function-major within a level, frequency order within a level)."""
+    names = sorted(FX_BASE.items(), key=lambda kv: kv[1])
+    name, base = max(((n, b) for n, b in names if b <= op), key=lambda nb: nb[1])
+    order = [n for n, _ in LEVEL_FORMS + MEM_FORMS].index(name)
+    if name in dict(MEM_FORMS):
+        sub, lvl = op - base, NREG
+    else:
+        sub, lvl = divmod(op - base, NREG)
+    cold = name in ("UN", "UNV", "UNC", "UN_M", "UNV_M", "UNC_M") and UNA[sub] == F_TAN
+    return (1 if cold else 0, lvl, order, sub)
+
+
 class Gen:
     def __init__(self, K: int, modi: bool):
         self.K = K
         self.modi = modi
         self.lines: list[str] = []
         self.defined: set[int] = set()
+        self.chunks: list = []
 
     def e(self, s: str):
         self.lines.append(s)
@@ -254,9 +274,12 @@ class Gen:
         """Label C<op>, its body, then back to the dispatch (or on to case `then`)."""
         assert op not in self.defined
         self.defined.add(op)
+        start = len(self.lines)
         self.e(f"C{op}:")
         body()
         self.e(f"bra.uni C{then};" if then is not None else "bra.uni LOOP;")
+        self.chunks.append((layout_key(op), self.lines[start:]))
+        del self.lines[start:]
 
     def build(self) -> str:
         K = self.K
@@ -433,6 +456,9 @@ class Gen:
                 self.case(fx("MS_M", f, 0), msm)
                 self.case(fx("SM_M", f, 0), smm)
 
+        # the cases in code order (see layout_key)
+        for _, chunk in sorted(self.chunks, key=lambda c: c[0]):
+            self.lines.extend(chunk)
         # opcodes the stage compiler never emits for this kernel: end with NaN
         self.e("CBAD:")
         for j in range(K):
