@@ -122,7 +122,7 @@ bool choose_shape(long long P, long long D, int F, int O, int max_len, const tgp
       const size_t per_cta = limit / ctas - 1024;
       const int tp_min = ctas > 2 ? 2 * CH : CH, bt_min = ctas > 2 ? 8 : 4;
       while (bytes() > per_cta && s.tp > tp_min && !(cfg && cfg->points_per_tile)) s.tp /= 2;
-      while (bytes() > per_cta && s.bt > bt_min && !(cfg && cfg->trees_per_block)) s.bt /= 2;
+      while (bytes() > per_cta && s.bt > bt_min && !(cfg && cfg->trees_per_block)) --s.bt;
       fit = bytes() <= per_cta;
     }
   }

@@ -20,6 +20,7 @@
 //      groups in order and divides by D.
 //   Forward mode writes every output point instead.
 #include "tgp_internal.cuh"
+#include "isa_fwd.cuh"
 #include "interp_fwd.cuh"
 
 namespace tgp {
@@ -99,7 +100,7 @@ __device__ __forceinline__ int pt_index(int lane, int j) {
 
 // ----------------------------------------------------------- smem layout
 struct EvalSmem {
-  size_t prog, xs, ys, mo, cpart, tacc, order, lens, misc, total;
+  size_t prog, xs, ys, mo, stk, cpart, tacc, order, lens, misc, total;
   int xs_stride;
 };
 
@@ -114,6 +115,7 @@ __host__ __device__ inline EvalSmem eval_smem_layout(int K, int nw, bool modi, b
   L.xs = off; off = align_up(off + (size_t)F * L.xs_stride * 4, 16);
   L.ys = off; off = align_up(off + (mse ? (size_t)O * tp * 4 : 0), 16);
   L.mo = off; off = align_up(off + (modi ? (size_t)nw * O * 32 * K * 4 : 0), 16);
+  L.stk = off; off = align_up(off + (size_t)nw * fx::NSM * 32 * K * 4, 16);  // memory-stack rows
   int cpt = tp / (32 * K);
   L.cpart = off; off = align_up(off + (size_t)bt * cpt * O * 4, 16);
   L.tacc = off; off = align_up(off + (size_t)bt * O * 8, 16);
@@ -177,6 +179,7 @@ __global__ void __launch_bounds__(NW * 32, 3) eval_kernel(const __grid_constant_
     float* xs = reinterpret_cast<float*>(smem + lay.xs);
     float* ys = reinterpret_cast<float*>(smem + lay.ys);
     float* mo = reinterpret_cast<float*>(smem + lay.mo) + warp * a.O * CH;
+    float* stk = reinterpret_cast<float*>(smem + lay.stk) + warp * fx::NSM * CH;
     float* cpart = reinterpret_cast<float*>(smem + lay.cpart);
     double* tacc = reinterpret_cast<double*>(smem + lay.tacc);
     int* order = reinterpret_cast<int*>(smem + lay.order);
@@ -282,7 +285,7 @@ __global__ void __launch_bounds__(NW * 32, 3) eval_kernel(const __grid_constant_
           }
           modi_out = interp_fwd<K, MODI>(smem_u32(prog_s + (size_t)t * a.pcap),
                                           smem_u32(xs + qbase + 4 * lane), (unsigned)XS * 4u,
-                                          smem_u32(mo + 4 * lane), res) != 0;
+                                          smem_u32(mo + 4 * lane), smem_u32(stk + 4 * lane), res) != 0;
         }
         for (int oo = 0; oo < O; ++oo) {
           float v[K];

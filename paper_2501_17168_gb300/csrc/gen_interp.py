@@ -9,8 +9,9 @@ are both subtrees evaluates the child that needs more levels first into G[d]
 and the other into G[d+1] (Sethi-Ullman order), then combines them into
 G[d].  Nothing is ever copied between groups, so evaluation order costs no
 moves.  Levels 0..NREG-1 are registers; deeper nesting (trees whose
-Sethi-Ullman number exceeds NREG) saves G[NREG-1] to a per-thread memory
-stack of MAXS entries and combines with it later.
+Sethi-Ullman number exceeds NREG) saves G[NREG-1] on a memory stack and
+combines with it later (the first NSM entries in per-warp shared-memory
+rows, deeper ones in local memory).
 Leaves never get an instruction of their own: a leaf operand rides in its
 parent's word (feature index or constant bits), and a binary node with two
 leaf children is one instruction (two words when the operands need more than
@@ -85,7 +86,7 @@ MAGIC = fhex(12582912.0)      # 1.5 * 2^23: x + MAGIC - MAGIC = rint(x) for |x| 
 
 # ------------------------------------------------------------------ forward ISA
 NREG = 3          # nesting levels held in registers
-MAXS = 6          # memory-stack entries: trees of <= 1024 nodes need <= 9 levels
+MAXS = 6          # local-memory stack entries: trees of <= 1024 nodes need <= 9 levels
 NC = [F_SUB, F_PDIV]   # non-commutative binary functions (max is symmetric in PTX)
 
 # (name, number of sub-forms); level forms come first, then memory forms
@@ -102,10 +103,14 @@ LEVEL_FORMS = [
     ("BV_M", 5), ("BC_M", 5), ("RV_M", 5), ("RC_M", 5),
     ("BS_M", 5), ("RS_M", 5),
 ]
+NSM = 1           # memory-stack entries held in shared memory (the deeper ones in local memory)
 MEM_FORMS = [
-    ("SAVE", 1),                                  # push G[NREG-1]
+    ("SAVE", 1),                                  # push G[NREG-1] (local memory)
     ("MS", 5), ("SM", 2),                         # pop m: G = f(m, G) / f(G, m)  (G = G[NREG-1])
     ("MS_M", 5), ("SM_M", 5),
+    ("SAVES", NSM),                               # the same for entry s < NSM in shared memory
+    ("MSS", 5 * NSM), ("SMS", 2 * NSM),           #   (sub = f * NSM + s)
+    ("MSS_M", 5 * NSM), ("SMS_M", 5 * NSM),
 ]
 
 
@@ -271,14 +276,28 @@ class Gen:
             self.e(f"st.shared.v4.f32 [r_ma{off}], {{{', '.join(regs)}}};")
 
     def case(self, op, body, then=None):
-        """Label C<op>, its body, then back to the dispatch (or on to case `then`)."""
+        """Label C<op>, its body, then back to the dispatch (or on to `then`:
+        another case's opcode or a body label)."""
         assert op not in self.defined
         self.defined.add(op)
         start = len(self.lines)
         self.e(f"C{op}:")
         body()
-        self.e(f"bra.uni C{then};" if then is not None else "bra.uni LOOP;")
+        if then is None:
+            self.e("bra.uni LOOP;")
+        else:
+            self.e(f"bra.uni {then};" if isinstance(then, str) else f"bra.uni C{then};")
         self.chunks.append((layout_key(op), self.lines[start:]))
+        del self.lines[start:]
+
+    def body(self, label, body):
+        """A combining body reached only by bra from cases; placed with the
+        memory-stack cases."""
+        start = len(self.lines)
+        self.e(f"{label}:")
+        body()
+        self.e("bra.uni LOOP;")
+        self.chunks.append(((0, NREG, -1, len(self.chunks)), self.lines[start:]))
         del self.lines[start:]
 
     def build(self) -> str:
@@ -294,9 +313,10 @@ class Gen:
         self.e(".reg .f32 " + ", ".join(G(d)(j) for d in range(NREG) for j in range(K)) + ";")
         self.e(".reg .pred " + ", ".join(f"P{j}" for j in range(K)) + ";")
         self.e(".reg .u32 r_ptr, r_ix, r_iy, r_nx, r_ny, r_op, r_ad, r_xc, r_xstr, r_mo, r_moo, "
-               "r_ma, r_flag, r_t, r_sp;")
+               "r_ma, r_flag, r_t, r_sp, r_sb;")
         self.e(f".local .align 16 .b8 gm[{MAXS * K * 4}];")
         self.e("mov.u32 r_sp, gm;")
+        self.e("mov.u32 r_sb, %{sb};")
         self.e("mov.u32 r_ptr, %{pg};")
         self.e("mov.u32 r_xc, %{xc};")
         self.e("mov.u32 r_xstr, %{xstr};")
@@ -434,27 +454,53 @@ class Gen:
                     self.case(fx("BS_M", f, d), bsm)
                     self.case(fx("RS_M", f, d), rsm)
 
+        # memory stack: entry s < NSM in the warp's shared-memory rows, deeper
+        # entries in local memory; a pop loads the entry into L and goes on
+        # in a combining body shared by both kinds of entry
         Gt = G(top)
+        sm_off = lambda q, h: f"[r_sb+{q * 128 * K + 512 * h}]"
+
+        def sm_push(q):
+            for h in range(K // 4):
+                regs = ", ".join(Gt(4 * h + i) for i in range(4))
+                self.e(f"st.shared.v4.f32 {sm_off(q, h)}, {{{regs}}};")
+
+        def sm_pop(q):
+            for h in range(K // 4):
+                regs = ", ".join(L(4 * h + i) for i in range(4))
+                self.e(f"ld.shared.v4.f32 {{{regs}}}, {sm_off(q, h)};")
+
         self.case(fx("SAVE", 0, 0), lambda: self.mem_push(Gt))
+        for q in range(NSM):
+            self.case(fx("SAVES", q, 0), lambda q=q: sm_push(q))
         for f in BIN:
-            self.case(fx("MS", f, 0), lambda f=f: (self.mem_pop(L), self.fn2(f, Gt, L, Gt)))
+            self.body(f"MSB{f}", lambda f=f: self.fn2(f, Gt, L, Gt))
+            self.case(fx("MS", f, 0), lambda: self.mem_pop(L), then=f"MSB{f}")
+            for q in range(NSM):
+                self.case(fx("MSS", f * NSM + q, 0), lambda q=q: sm_pop(q), then=f"MSB{f}")
         for i, f in enumerate(NC):
-            self.case(fx("SM", i, 0), lambda f=f: (self.mem_pop(L), self.fn2(f, Gt, Gt, L)))
+            self.body(f"SMB{i}", lambda f=f: self.fn2(f, Gt, Gt, L))
+            self.case(fx("SM", i, 0), lambda: self.mem_pop(L), then=f"SMB{i}")
+            for q in range(NSM):
+                self.case(fx("SMS", i * NSM + q, 0), lambda q=q: sm_pop(q), then=f"SMB{i}")
         if self.modi:
             for f in BIN:
                 def msm(f=f):
-                    self.mem_pop(L)
                     self.fn2(f, T, L, Gt)
                     self.modi_add(T)
 
                 def smm(f=f):
-                    self.mem_pop(L)
                     self.fn2(f, T, Gt, L)
                     self.modi_add(T)
                     self.movs(Gt, L)
 
-                self.case(fx("MS_M", f, 0), msm)
-                self.case(fx("SM_M", f, 0), smm)
+                self.body(f"MSMB{f}", msm)
+                self.body(f"SMMB{f}", smm)
+                self.case(fx("MS_M", f, 0), lambda: self.mem_pop(L), then=f"MSMB{f}")
+                self.case(fx("SM_M", f, 0), lambda: self.mem_pop(L), then=f"SMMB{f}")
+                for q in range(NSM):
+                    self.case(fx("MSS_M", f * NSM + q, 0), lambda q=q: sm_pop(q), then=f"MSMB{f}")
+                    self.case(fx("SMS_M", f * NSM + q, 0), lambda q=q: sm_pop(q), then=f"SMMB{f}")
 
         # the cases in code order (see layout_key)
         for _, chunk in sorted(self.chunks, key=lambda c: c[0]):
@@ -479,7 +525,7 @@ class Gen:
 
 
 def operand_map(K):
-    names = [f"a{j}" for j in range(K)] + ["flag", "pg", "xc", "xstr", "mo"]
+    names = [f"a{j}" for j in range(K)] + ["flag", "pg", "xc", "xstr", "mo", "sb"]
     return {n: i for i, n in enumerate(names)}
 
 
@@ -491,10 +537,10 @@ def render(K: int, modi: bool) -> str:
     # C string literal, one PTX line per source line
     lit = "\n".join('      "' + l.replace("\\", "\\\\").replace('"', '\\"') + '\\n"' for l in body.split("\n"))
     outs = ", ".join([f'"=f"(acc[{j}])' for j in range(K)] + ['"=r"(flag)'])
-    ins = '"r"(pg), "r"(xc), "r"(xstr), "r"(mo)'
+    ins = '"r"(pg), "r"(xc), "r"(xstr), "r"(mo), "r"(sb)'
     return f"""template <>
 __device__ __forceinline__ unsigned interp_fwd<{K}, {'true' if modi else 'false'}>(
-    unsigned pg, unsigned xc, unsigned xstr, unsigned mo, float (&acc)[{K}]) {{
+    unsigned pg, unsigned xc, unsigned xstr, unsigned mo, unsigned sb, float (&acc)[{K}]) {{
   unsigned flag;
   asm volatile(
 {lit}
@@ -510,7 +556,8 @@ def render_isa() -> str:
     out = [
         "// isa_fwd.cuh -- GENERATED by gen_interp.py; do not edit by hand.",
         "// Opcodes of the forward instruction set run by interp_fwd (level registers",
-        "// G[0..NREG-1], a per-thread memory stack of MAXS entries).  A level form's",
+        "// G[0..NREG-1], a memory stack of NSM shared-memory entries per warp and",
+        "// MAXS local-memory entries per thread).  A level form's",
         "// opcode is base + sub * NREG + d, a memory form's base + sub; sub is the",
         "// unary index f - F_SIN, the binary function f, or for the forms that exist",
         "// only for non-commutative functions nc_index(f).  Word: .x = opcode |",
@@ -523,6 +570,7 @@ def render_isa() -> str:
         "namespace fx {",
         f"constexpr int NREG = {NREG};",
         f"constexpr int MAXS = {MAXS};",
+        f"constexpr int NSM = {NSM};   // stack entries in shared memory (SAVES/MSS/SMS forms)",
         "enum : uint32_t {",
         "  END_ROOT = 0,  // output := G[0] (one output, no Modi node)",
         "  END_MODI = 1,  // outputs are the Modi accumulators",
@@ -542,16 +590,17 @@ def main():
     parts = [
         "// interp_fwd.cuh -- GENERATED by gen_interp.py; do not edit by hand.",
         "// Forward interpreter loop of the level-register machine (isa_fwd.cuh).",
-        "// interp_fwd<K, MODI>(pg, xc, xstr, mo, acc): pg = shared address of the",
-        "// program, xc = shared address of the lane's first point of feature 0,",
+        "// interp_fwd<K, MODI>(pg, xc, xstr, mo, sb, acc): pg = shared address of",
+        "// the program, xc = shared address of the lane's first point of feature 0,",
         "// xstr = bytes between feature rows, mo = shared address of the lane's Modi",
-        "// accumulators; returns 1 when the outputs are the Modi sums, else 0 with",
-        "// the single output in acc.",
+        "// accumulators, sb = shared address of the lane's 16 bytes in the warp's",
+        "// memory-stack rows (NSM entries of K*128 bytes); returns 1 when the",
+        "// outputs are the Modi sums, else 0 with the single output in acc.",
         "#pragma once",
         "namespace tgp {",
         "template <int K, bool MODI>",
         "__device__ __forceinline__ unsigned interp_fwd(unsigned pg, unsigned xc, unsigned xstr,",
-        "                                               unsigned mo, float (&acc)[K]);",
+        "                                               unsigned mo, unsigned sb, float (&acc)[K]);",
     ]
     for K, modi in ((8, False), (4, False), (4, True), (8, True)):
         parts.append(render(K, modi))

@@ -1,6 +1,7 @@
 // isa_fwd.cuh -- GENERATED by gen_interp.py; do not edit by hand.
 // Opcodes of the forward instruction set run by interp_fwd (level registers
-// G[0..NREG-1], a per-thread memory stack of MAXS entries).  A level form's
+// G[0..NREG-1], a memory stack of NSM shared-memory entries per warp and
+// MAXS local-memory entries per thread).  A level form's
 // opcode is base + sub * NREG + d, a memory form's base + sub; sub is the
 // unary index f - F_SIN, the binary function f, or for the forms that exist
 // only for non-commutative functions nc_index(f).  Word: .x = opcode |
@@ -13,6 +14,7 @@ namespace tgp {
 namespace fx {
 constexpr int NREG = 3;
 constexpr int MAXS = 6;
+constexpr int NSM = 1;   // stack entries in shared memory (SAVES/MSS/SMS forms)
 enum : uint32_t {
   END_ROOT = 0,  // output := G[0] (one output, no Modi node)
   END_MODI = 1,  // outputs are the Modi accumulators
@@ -45,7 +47,12 @@ enum : uint32_t {
   SM = 308,
   MS_M = 310,
   SM_M = 315,
-  COUNT = 320
+  SAVES = 320,
+  MSS = 321,
+  SMS = 326,
+  MSS_M = 328,
+  SMS_M = 333,
+  COUNT = 338
 };
 // index of a non-commutative binary function among the two-entry forms
 __host__ __device__ constexpr int nc_index(int f) { return f == 1 ? 0 : f == 3 ? 1 : -1; }

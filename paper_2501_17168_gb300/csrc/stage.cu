@@ -125,7 +125,7 @@ __device__ int compile_fx(NodeSmem& ns, bool single_out, uint2* prog, int cap) {
         const bool mem = lv + 1 >= NREG;
         if (n == first) {  // first operand done: evaluate the second one
           if (mem) {
-            if (sdepth >= MAXS || !put(SAVE, 0)) return -1;
+            if (sdepth >= NSM + MAXS || !put(sdepth < NSM ? SAVES + sdepth : SAVE, 0)) return -1;
             ++sdepth;
             ns.slot[second] = lv;
           } else {
@@ -141,11 +141,21 @@ __device__ int compile_fx(NodeSmem& ns, bool single_out, uint2* prog, int cap) {
           else if (nc < 0) x = BS + f * NREG + lv;
           else x = RS + nc * NREG + lv;
         } else {  // first operand on the memory stack, second in G[NREG-1]
-          --sdepth;
-          if (a_first) x = (modi ? MS_M : MS) + f;
-          else if (modi) x = SM_M + f;
-          else if (nc < 0) x = MS + f;
-          else x = SM + nc;
+          const int sq = --sdepth;
+          if (sq < NSM) {  // entry in the warp's shared-memory rows
+            if (a_first) x = (modi ? MSS_M : MSS) + f * NSM + sq;
+            else if (modi) x = SMS_M + f * NSM + sq;
+            else if (nc < 0) x = MSS + f * NSM + sq;
+            else x = SMS + nc * NSM + sq;
+          } else if (a_first) {
+            x = (modi ? MS_M : MS) + f;
+          } else if (modi) {
+            x = SM_M + f;
+          } else if (nc < 0) {
+            x = MS + f;
+          } else {
+            x = SM + nc;
+          }
         }
       }
     }
