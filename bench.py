@@ -443,7 +443,7 @@ def suite_lines(dev, steps):
     for bp in bps:
         tt, vv, ss, Xp, yp = bp.tensors
         cands = [c for c in autotune.candidates(bp.pop.pop, bp.data.n_points, 1)
-                 if c["points_per_lane"] == 8 and c["trees_per_block"] >= 4]
+                 if c.get("points_per_lane", 8) == 8 and c.get("trees_per_block", 16) >= 4]
         best, _ = autotune.tune(tt, vv, ss, Xp, yp, 1, max_len=bp.pop.max_len, reps=2, cands=cands,
                                 store=False)
         tuned.append(api.BatchProblem(tt, vv, ss, Xp, yp, 1, max_len=bp.pop.max_len, config=best))

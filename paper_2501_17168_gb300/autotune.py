@@ -40,7 +40,7 @@ def _key(device, P, D, F, O, max_len) -> str:
 
 
 def candidates(P: int, D: int, O: int = 1):
-    out = []
+    out = [{}]  # the library's own shape heuristic
     for K in ((4,) if O > 1 else (8, 4)):
         ch = 32 * K
         for tp_mult in (1, 2, 4, 8):
@@ -87,7 +87,7 @@ def tune(type_, val, size, X, y, n_outputs=1, max_len=None, reps=3, cands=None, 
     table = []
     for cfg in cands:
         try:
-            api.tgp_fitness_mse(type_, val, size, X, y, n_outputs, max_len=max_len, config=cfg)
+            api.tgp_fitness_mse(type_, val, size, X, y, n_outputs, max_len=max_len, config=cfg or None)
         except Exception:  # shape not supported (shared memory): skip
             continue
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

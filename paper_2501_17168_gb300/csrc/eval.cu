@@ -115,7 +115,7 @@ __host__ __device__ inline EvalSmem eval_smem_layout(int K, int nw, bool modi, b
   L.xs = off; off = align_up(off + (size_t)F * L.xs_stride * 4, 16);
   L.ys = off; off = align_up(off + (mse ? (size_t)O * tp * 4 : 0), 16);
   L.mo = off; off = align_up(off + (modi ? (size_t)nw * O * 32 * K * 4 : 0), 16);
-  L.stk = off; off = align_up(off + (size_t)nw * fx::NSM * 32 * K * 4, 16);  // memory-stack rows
+  L.stk = off; off = align_up(off + (modi ? 0 : (size_t)nw * fx::NSM * 32 * K * 4), 16);  // memory-stack rows
   int cpt = tp / (32 * K);
   L.cpart = off; off = align_up(off + (size_t)bt * cpt * O * 4, 16);
   L.tacc = off; off = align_up(off + (size_t)bt * O * 8, 16);

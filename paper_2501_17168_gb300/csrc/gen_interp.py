@@ -460,12 +460,19 @@ class Gen:
         Gt = G(top)
         sm_off = lambda q, h: f"[r_sb+{q * 128 * K + 512 * h}]"
 
+        # (the Modi kernel keeps the whole stack in local memory: its shared
+        # memory holds the Modi accumulators; the order of pushes and pops is
+        # the same, so the shared-memory forms become local pushes and pops)
         def sm_push(q):
+            if self.modi:
+                return self.mem_push(Gt)
             for h in range(K // 4):
                 regs = ", ".join(Gt(4 * h + i) for i in range(4))
                 self.e(f"st.shared.v4.f32 {sm_off(q, h)}, {{{regs}}};")
 
         def sm_pop(q):
+            if self.modi:
+                return self.mem_pop(L)
             for h in range(K // 4):
                 regs = ", ".join(L(4 * h + i) for i in range(4))
                 self.e(f"ld.shared.v4.f32 {{{regs}}}, {sm_off(q, h)};")
@@ -570,7 +577,8 @@ def render_isa() -> str:
         "namespace fx {",
         f"constexpr int NREG = {NREG};",
         f"constexpr int MAXS = {MAXS};",
-        f"constexpr int NSM = {NSM};   // stack entries in shared memory (SAVES/MSS/SMS forms)",
+        f"constexpr int NSM = {NSM};   // stack entries in shared memory (SAVES/MSS/SMS forms; the",
+        "                           // Modi kernel keeps them in local memory)",
         "enum : uint32_t {",
         "  END_ROOT = 0,  // output := G[0] (one output, no Modi node)",
         "  END_MODI = 1,  // outputs are the Modi accumulators",

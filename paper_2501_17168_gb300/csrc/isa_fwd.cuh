@@ -14,7 +14,8 @@ namespace tgp {
 namespace fx {
 constexpr int NREG = 3;
 constexpr int MAXS = 6;
-constexpr int NSM = 1;   // stack entries in shared memory (SAVES/MSS/SMS forms)
+constexpr int NSM = 1;   // stack entries in shared memory (SAVES/MSS/SMS forms; the
+                           // Modi kernel keeps them in local memory)
 enum : uint32_t {
   END_ROOT = 0,  // output := G[0] (one output, no Modi node)
   END_MODI = 1,  // outputs are the Modi accumulators

@@ -229,6 +229,21 @@ def test_leaves_only_and_long_trees(orc):
     check_forward(orc, W.Population(p.type, p.val, p.size, 1024), X, min_strict=0.5)
 
 
+def test_deep_modi_trees_use_every_stack_level(orc):
+    # full binary Modi trees of 511 nodes need 8 register levels: three in
+    # registers, the shared-memory stack entry and local-memory entries, with
+    # Modi nodes (and their stack-combining forms) at every depth
+    p = W.random_population(14, 6, 511, (511, 511), max_depth=8, n_features=3, n_outputs=3,
+                            modi=True, modi_max=16, fset=(0, 1, 2, 3, 4))
+    X = np.random.default_rng(11).uniform(-1, 1, (500, 3)).astype(np.float32)
+    check_forward(orc, p, X, O=3, min_strict=0.5)
+    y = np.random.default_rng(12).standard_normal((500, 3)).astype(np.float32)
+    m, st = gpu_mse(p, X, y, O=3)
+    ref, allow, ost = orc.mse(p.type, p.val, p.size, X, y, n_outputs=3, rel_tol=1e-5)
+    r = compare_mse(m, ref, allow)
+    assert len(r["failed"]) == 0 and len(r["class_mismatch"]) == 0, r
+
+
 def test_empty_population_and_points():
     p = W.random_population(3, 5, 10, n_features=2)
     X0 = np.zeros((0, 2), np.float32)
