@@ -77,7 +77,8 @@ enum {
   TGP_TREE_MODI = 16,   /* Modi output index not in [0, n_outputs)               */
   TGP_TREE_CONST = 32,  /* constant not finite                                   */
   TGP_TREE_SIZE = 64,   /* subtree sizes disagree with the prefix structure      */
-  TGP_TREE_DEPTH = 128  /* needs more evaluation registers than the kernel has   */
+  TGP_TREE_DEPTH = 128  /* nests deeper than the evaluation registers and stack
+                           hold (never for trees of up to 1024 nodes)           */
 };
 
 /* Library limits. */

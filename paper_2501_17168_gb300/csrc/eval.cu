@@ -11,7 +11,9 @@
 //      feature-major [F][tp] so a lane reads its points with 16-byte loads)
 //      and the targets;
 //   3. the warps pull (tree, 32*K-point chunk) sub-items, longest program
-//      first, and run the tree's program over the chunk (K points per lane);
+//      first, and run the tree's program over the chunk (K points per lane;
+//      the interpreter's first memory-stack entry is a per-warp row of
+//      shared memory, deeper entries are in local memory);
 //   4. MSE mode: each chunk's squared residuals are summed in FP32 per lane
 //      and across the warp with shuffles; chunk sums are folded into FP64
 //      per-tree accumulators in a fixed order, so the result does not depend
