@@ -9,7 +9,7 @@
 #include "tgp_internal.cuh"
 
 namespace tgp {
-size_t stage_smem_bytes();
+size_t stage_smem_bytes(int lmax);
 int stage_threads();
 const void* stage_kernel_ptr();
 const void* find_eval_kernel(int K, int nw, bool modi, bool out);
@@ -246,8 +246,11 @@ tgp_status launch_stage(Planned* qs, int n, char* ws, cudaStream_t st, const Dev
   }
   if (m == 0) return TGP_OK;
   b.n = m;
+  int lmax = 16;
+  for (int i = 0; i < m; ++i) lmax = b.p[i].max_len > lmax ? b.p[i].max_len : lmax;
+  b.lmax = (lmax + 15) & ~15;
   const void* fn = stage_kernel_ptr();
-  size_t smem = stage_smem_bytes();
+  size_t smem = stage_smem_bytes(b.lmax);
   if (!ensure_smem(fn, smem)) return TGP_ERR_CUDA;
   const int warps_per_cta = stage_threads() / 32;
   long long grid = cdiv(total, warps_per_cta);

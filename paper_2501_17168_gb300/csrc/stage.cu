@@ -16,15 +16,29 @@
 
 namespace tgp {
 
-// per-warp shared memory: node records of one tree
+// per-warp shared memory: node records of one tree, lmax entries per array
+// (lmax = the longest max_len of the launch, a multiple of 16)
 struct NodeSmem {
-  uint32_t info[MAX_LEN];   // bits 0-3 func, 4-5 kind (0 var,1 const,2 unary,3 binary), 6 modi, 8-15 out
-  uint32_t leaf[MAX_LEN];   // variable index or constant bits
-  int16_t sz[MAX_LEN];      // subtree size (0 = not a valid size)
-  int16_t par[MAX_LEN];     // parent index
-  uint8_t need[MAX_LEN];    // registers the subtree needs (acc + slots)
-  uint8_t slot[MAX_LEN];    // first free slot when the subtree is evaluated
+  uint32_t* info;   // bits 0-3 func, 4-5 kind (0 var,1 const,2 unary,3 binary), 6 modi, 8-15 out
+  uint32_t* leaf;   // variable index or constant bits
+  int16_t* sz;      // subtree size (0 = not a valid size)
+  int16_t* par;     // parent index
+  uint8_t* need;    // registers (levels) the subtree needs
+  uint8_t* slot;    // the subtree's level (first free slot for the adjoint set)
 };
+
+__host__ __device__ constexpr size_t node_smem_bytes(int lmax) { return (size_t)lmax * 14; }
+
+__device__ NodeSmem node_smem(unsigned char* base, int lmax) {
+  NodeSmem ns;
+  ns.info = reinterpret_cast<uint32_t*>(base);
+  ns.leaf = ns.info + lmax;
+  ns.sz = reinterpret_cast<int16_t*>(ns.leaf + lmax);
+  ns.par = ns.sz + lmax;
+  ns.need = reinterpret_cast<uint8_t*>(ns.par + lmax);
+  ns.slot = ns.need + lmax;
+  return ns;
+}
 
 constexpr int STAGE_WARPS = 4;
 
@@ -278,7 +292,7 @@ __device__ int compile_adj(NodeSmem& ns, bool single_out, uint2* prog) {
 __global__ void __launch_bounds__(STAGE_WARPS * 32) stage_kernel(const __grid_constant__ StageBatch b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  NodeSmem& ns = reinterpret_cast<NodeSmem*>(smem_raw)[warp];
+  NodeSmem ns = node_smem(smem_raw + (size_t)warp * node_smem_bytes(b.lmax), b.lmax);
   const long long total = b.end[b.n - 1];
 
   for (long long gt = (long long)blockIdx.x * STAGE_WARPS + warp; gt < total;
@@ -414,7 +428,7 @@ __global__ void __launch_bounds__(STAGE_WARPS * 32) stage_kernel(const __grid_co
   }
 }
 
-size_t stage_smem_bytes() { return sizeof(NodeSmem) * STAGE_WARPS; }
+size_t stage_smem_bytes(int lmax) { return node_smem_bytes(lmax) * STAGE_WARPS; }
 int stage_threads() { return STAGE_WARPS * 32; }
 const void* stage_kernel_ptr() { return (const void*)stage_kernel; }
 

@@ -194,6 +194,7 @@ constexpr int MAX_PROBLEMS = 16;
 
 struct StageBatch {
   int n;
+  int lmax;                          // node records per warp: max max_len, multiple of 16
   long long end[MAX_PROBLEMS];       // cumulative tree counts
   StageArgs p[MAX_PROBLEMS];
 };
