@@ -93,7 +93,7 @@ bool choose_shape(long long P, long long D, int F, int O, int max_len, const tgp
   if (s.K != 4 && s.K != 8) return false;
   const int CH = 32 * s.K;
   const int pcap = pcap_of(max_len);
-  s.bt = (cfg && cfg->trees_per_block) ? cfg->trees_per_block : 16;
+  s.bt = (cfg && cfg->trees_per_block) ? cfg->trees_per_block : 32;
   if (s.bt < 1 || s.bt > 64) return false;
   const long long Dr = D < 1 ? 1 : D;
   if (cfg && cfg->points_per_tile) {

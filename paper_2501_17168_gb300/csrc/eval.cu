@@ -102,17 +102,28 @@ __device__ __forceinline__ int pt_index(int lane, int j) {
 
 // ----------------------------------------------------------- smem layout
 struct EvalSmem {
-  size_t prog, xs, ys, mo, stk, cpart, tacc, order, lens, misc, total;
+  size_t prog, xs, ys, mo, stk, cpart, tacc, order, lens, poff, misc, total;
   int xs_stride;
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Words of the shared-memory program area of a block of bt trees: the
+// programs are packed back to back; a block whose programs do not fit is
+// evaluated in rounds (compiled programs average well below their capacity
+// pcap, so one round is the rule).  Two words of padding follow the area
+// (the interpreter prefetches the word after a program's end).
+__host__ __device__ inline int prog_area_words(int bt, int pcap) {
+  const long long full = (long long)bt * pcap;
+  const long long half = full / 2 + pcap;
+  return (int)((full < half ? full : half) + 1) & ~1;
+}
+
 __host__ __device__ inline EvalSmem eval_smem_layout(int K, int nw, bool modi, bool mse, int bt,
                                                      int pcap, int tp, int F, int O) {
   EvalSmem L;
   size_t off = 0;
-  L.prog = off; off = align_up(off + (size_t)bt * pcap * 8, 16);
+  L.prog = off; off = align_up(off + ((size_t)prog_area_words(bt, pcap) + 2) * 8, 16);
   L.xs_stride = tp + 4;
   L.xs = off; off = align_up(off + (size_t)F * L.xs_stride * 4, 16);
   L.ys = off; off = align_up(off + (mse ? (size_t)O * tp * 4 : 0), 16);
@@ -123,6 +134,7 @@ __host__ __device__ inline EvalSmem eval_smem_layout(int K, int nw, bool modi, b
   L.tacc = off; off = align_up(off + (size_t)bt * O * 8, 16);
   L.order = off; off = align_up(off + (size_t)bt * 4, 16);
   L.lens = off; off = align_up(off + (size_t)bt * 4, 16);
+  L.poff = off; off = align_up(off + (size_t)bt * 4, 16);
   L.misc = off; off = align_up(off + 64, 16);
   L.total = off;
   return L;
@@ -186,6 +198,9 @@ __global__ void __launch_bounds__(NW * 32, 3) eval_kernel(const __grid_constant_
     double* tacc = reinterpret_cast<double*>(smem + lay.tacc);
     int* order = reinterpret_cast<int*>(smem + lay.order);
     int* lens = reinterpret_cast<int*>(smem + lay.lens);
+    int* poff = reinterpret_cast<int*>(smem + lay.poff);
+    int* s_r1 = reinterpret_cast<int*>(smem + lay.misc);
+    const int pw = prog_area_words(a.bt, a.pcap);
     const int XS = lay.xs_stride;
     const int cpt = a.tp / CH;
     const int O = a.O;
@@ -194,146 +209,159 @@ __global__ void __launch_bounds__(NW * 32, 3) eval_kernel(const __grid_constant_
     const long long t0 = blk * a.bt;
     const int nt = (int)min((long long)a.bt, a.pop - t0);
 
-    // 1. stage the block's programs
-    if (tid == 0) {
-      fence_proxy_async_smem();
-      uint32_t bytes = 0;
-      for (int t = 0; t < nt; ++t) bytes += (uint32_t)((a.plen[t0 + t] + 1) & ~1) * 8u;
-      mbar_arrive_expect_tx(mbar, bytes);
-      for (int t = 0; t < nt; ++t) {
-        int L = a.plen[t0 + t];
-        if (L > 0)
-          bulk_g2s(prog_s + (size_t)t * a.pcap, a.prog + (size_t)(t0 + t) * a.pcap,
-                   (uint32_t)((L + 1) & ~1) * 8u, mbar);
-      }
-    }
-    // longest program first
-    for (int t = tid; t < nt; t += NW * 32) {
-      int Lt = a.plen[t0 + t];
-      int rank = 0;
-      for (int u = 0; u < nt; ++u) {
-        int Lu = a.plen[t0 + u];
-        rank += (Lu > Lt) || (Lu == Lt && u < t);
-      }
-      order[rank] = t;
-      lens[t] = Lt;
-    }
     if (!OUT)
       for (int i = tid; i < nt * O; i += NW * 32) tacc[i] = 0.0;
-    if (!mbar_wait_bounded(mbar, phase, a.ctrl)) return;
-    phase ^= 1u;
-    __syncthreads();
-
-    for (int gi = 0; gi < a.g; ++gi) {
-      const long long tile = (long long)grp * a.g + gi;
-      if (tile >= a.n_tiles) break;
-      const long long p0 = tile * a.tp;
-      const int np = (int)min((long long)a.tp, a.D - p0);
-
-      // 2. X tile -> xs[f][q] (zero beyond D), targets -> ys[o][q]
-      {
-        const int fw = min(a.F, 32), rows = 32 / fw, rr = lane / fw, ff = lane - rr * fw;
-        for (int f0 = 0; f0 < a.F; f0 += 32) {
-          const int f = f0 + ff;
-          const bool act = rr < rows && f < a.F;
-#pragma unroll 4
-          for (int r0 = warp * rows; r0 < a.tp; r0 += NW * rows) {
-            const int q = r0 + rr;
-            if (act && q < a.tp) {
-              float v = 0.0f;
-              if (q < np) v = __ldg(a.X + (p0 + q) * a.ldx + f);
-              xs[f * XS + q] = v;
-            }
-          }
+    // rounds over the block: trees [r0, r1) whose programs fit the area
+    for (int r0 = 0; r0 < nt;) {
+      // 1. stage the round's programs, packed back to back
+      if (tid == 0) {
+        fence_proxy_async_smem();
+        int off = 0, r1 = r0;
+        for (; r1 < nt; ++r1) {
+          const int w = (a.plen[t0 + r1] + 1) & ~1;
+          if (r1 > r0 && off + w > pw) break;
+          poff[r1] = off;
+          off += w;
         }
-        if (!OUT) {
-          const int ow = min(O, 32), orows = 32 / ow, orr = lane / ow, off = lane - orr * ow;
-          const bool oact = orr < orows;
-#pragma unroll 4
-          for (int r0 = warp * orows; r0 < a.tp; r0 += NW * orows) {
-            const int q = r0 + orr;
-            if (oact && q < a.tp) {
-              float v = 0.0f;
-              if (q < np) v = __ldg(a.y + (p0 + q) * O + off);
-              ys[off * a.tp + q] = v;
-            }
-          }
-        }
-      }
-      if (tid == 0) *s_sub = 0;
-      __syncthreads();
-
-      // 3. sub-items: (tree, chunk), longest program first
-      const int nch = (np + CH - 1) / CH;
-      const int nsub = nt * nch;
-      for (;;) {
-        int s = 0;
-        if (lane == 0) s = atomicAdd(s_sub, 1);
-        s = __shfl_sync(0xffffffffu, s, 0);
-        if (s >= nsub) break;
-        const int t = order[s / nch];
-        const int ch = s - (s / nch) * nch;
-        const long long p = t0 + t;
-        const int qbase = ch * CH;
-        float res[K];
-        bool modi_out = false;
-        const bool valid = lens[t] > 0;
-        if (valid) {
-          if constexpr (MODI) {
-            float z[K];
-#pragma unroll
-            for (int j = 0; j < K; ++j) z[j] = 0.0f;
-            for (int oo = 0; oo < O; ++oo) st_pts<K>(mo + oo * CH + 4 * lane, z);
-          }
-          modi_out = interp_fwd<K, MODI>(smem_u32(prog_s + (size_t)t * a.pcap),
-                                          smem_u32(xs + qbase + 4 * lane), (unsigned)XS * 4u,
-                                          smem_u32(mo + 4 * lane), smem_u32(stk + 4 * lane), res) != 0;
-        }
-        for (int oo = 0; oo < O; ++oo) {
-          float v[K];
-          if (!valid) {
-#pragma unroll
-            for (int j = 0; j < K; ++j) v[j] = __int_as_float(0x7fc00000);
-          } else if (MODI && modi_out) {
-            ld_pts<K>(v, mo + oo * CH + 4 * lane);
-          } else {
-#pragma unroll
-            for (int j = 0; j < K; ++j) v[j] = oo == 0 ? res[j] : 0.0f;
-          }
-          if constexpr (OUT) {
-            float* dst = a.out + (p * O + oo) * a.D + p0;
-#pragma unroll
-            for (int j = 0; j < K; ++j) {
-              const int q = qbase + pt_index<K>(lane, j);
-              if (q < np) dst[q] = v[j];
-            }
-          } else {
-            float yv[K];
-            ld_pts<K>(yv, ys + oo * a.tp + qbase + 4 * lane);
-            float sse = 0.0f;
-#pragma unroll
-            for (int j = 0; j < K; ++j) {
-              const int q = qbase + pt_index<K>(lane, j);
-              const float r = __fsub_rn(v[j], yv[j]);
-              if (q < np) sse = fmaf(r, r, sse);
-            }
-#pragma unroll
-            for (int m = 16; m > 0; m >>= 1) sse += __shfl_xor_sync(0xffffffffu, sse, m);
-            if (lane == 0) cpart[(t * cpt + ch) * O + oo] = valid ? sse : 0.0f;
-          }
+        *s_r1 = r1;
+        mbar_arrive_expect_tx(mbar, (uint32_t)off * 8u);
+        for (int t = r0; t < r1; ++t) {
+          const int L = a.plen[t0 + t];
+          if (L > 0)
+            bulk_g2s(prog_s + poff[t], a.prog + (size_t)(t0 + t) * a.pcap, (uint32_t)((L + 1) & ~1) * 8u,
+                     mbar);
         }
       }
       __syncthreads();
-      // 4. fold chunk sums into the per-tree FP64 accumulators in chunk order
-      if (!OUT) {
-        for (int i = tid; i < nt * O; i += NW * 32) {
-          const int t = i / O, oo = i - (i / O) * O;
-          double acc = tacc[i];
-          for (int ch = 0; ch < nch; ++ch) acc += (double)cpart[(t * cpt + ch) * O + oo];
-          tacc[i] = acc;
+      const int r1 = *s_r1;
+      const int nr = r1 - r0;
+      // longest program first
+      for (int t = r0 + tid; t < r1; t += NW * 32) {
+        int Lt = a.plen[t0 + t];
+        int rank = 0;
+        for (int u = r0; u < r1; ++u) {
+          int Lu = a.plen[t0 + u];
+          rank += (Lu > Lt) || (Lu == Lt && u < t);
+        }
+        order[rank] = t;
+        lens[t] = Lt;
+      }
+      if (!mbar_wait_bounded(mbar, phase, a.ctrl)) return;
+      phase ^= 1u;
+      __syncthreads();
+
+      for (int gi = 0; gi < a.g; ++gi) {
+        const long long tile = (long long)grp * a.g + gi;
+        if (tile >= a.n_tiles) break;
+        const long long p0 = tile * a.tp;
+        const int np = (int)min((long long)a.tp, a.D - p0);
+
+        // 2. X tile -> xs[f][q] (zero beyond D), targets -> ys[o][q]
+        {
+          const int fw = min(a.F, 32), rows = 32 / fw, rr = lane / fw, ff = lane - rr * fw;
+          for (int f0 = 0; f0 < a.F; f0 += 32) {
+            const int f = f0 + ff;
+            const bool act = rr < rows && f < a.F;
+  #pragma unroll 4
+            for (int r0 = warp * rows; r0 < a.tp; r0 += NW * rows) {
+              const int q = r0 + rr;
+              if (act && q < a.tp) {
+                float v = 0.0f;
+                if (q < np) v = __ldg(a.X + (p0 + q) * a.ldx + f);
+                xs[f * XS + q] = v;
+              }
+            }
+          }
+          if (!OUT) {
+            const int ow = min(O, 32), orows = 32 / ow, orr = lane / ow, off = lane - orr * ow;
+            const bool oact = orr < orows;
+  #pragma unroll 4
+            for (int r0 = warp * orows; r0 < a.tp; r0 += NW * orows) {
+              const int q = r0 + orr;
+              if (oact && q < a.tp) {
+                float v = 0.0f;
+                if (q < np) v = __ldg(a.y + (p0 + q) * O + off);
+                ys[off * a.tp + q] = v;
+              }
+            }
+          }
+        }
+        if (tid == 0) *s_sub = 0;
+        __syncthreads();
+
+        // 3. sub-items: (tree, chunk), longest program first
+        const int nch = (np + CH - 1) / CH;
+        const int nsub = nr * nch;
+        for (;;) {
+          int s = 0;
+          if (lane == 0) s = atomicAdd(s_sub, 1);
+          s = __shfl_sync(0xffffffffu, s, 0);
+          if (s >= nsub) break;
+          const int t = order[s / nch];
+          const int ch = s - (s / nch) * nch;
+          const long long p = t0 + t;
+          const int qbase = ch * CH;
+          float res[K];
+          bool modi_out = false;
+          const bool valid = lens[t] > 0;
+          if (valid) {
+            if constexpr (MODI) {
+              float z[K];
+  #pragma unroll
+              for (int j = 0; j < K; ++j) z[j] = 0.0f;
+              for (int oo = 0; oo < O; ++oo) st_pts<K>(mo + oo * CH + 4 * lane, z);
+            }
+            modi_out = interp_fwd<K, MODI>(smem_u32(prog_s + poff[t]),
+                                            smem_u32(xs + qbase + 4 * lane), (unsigned)XS * 4u,
+                                            smem_u32(mo + 4 * lane), smem_u32(stk + 4 * lane), res) != 0;
+          }
+          for (int oo = 0; oo < O; ++oo) {
+            float v[K];
+            if (!valid) {
+  #pragma unroll
+              for (int j = 0; j < K; ++j) v[j] = __int_as_float(0x7fc00000);
+            } else if (MODI && modi_out) {
+              ld_pts<K>(v, mo + oo * CH + 4 * lane);
+            } else {
+  #pragma unroll
+              for (int j = 0; j < K; ++j) v[j] = oo == 0 ? res[j] : 0.0f;
+            }
+            if constexpr (OUT) {
+              float* dst = a.out + (p * O + oo) * a.D + p0;
+  #pragma unroll
+              for (int j = 0; j < K; ++j) {
+                const int q = qbase + pt_index<K>(lane, j);
+                if (q < np) dst[q] = v[j];
+              }
+            } else {
+              float yv[K];
+              ld_pts<K>(yv, ys + oo * a.tp + qbase + 4 * lane);
+              float sse = 0.0f;
+  #pragma unroll
+              for (int j = 0; j < K; ++j) {
+                const int q = qbase + pt_index<K>(lane, j);
+                const float r = __fsub_rn(v[j], yv[j]);
+                if (q < np) sse = fmaf(r, r, sse);
+              }
+  #pragma unroll
+              for (int m = 16; m > 0; m >>= 1) sse += __shfl_xor_sync(0xffffffffu, sse, m);
+              if (lane == 0) cpart[(t * cpt + ch) * O + oo] = valid ? sse : 0.0f;
+            }
+          }
         }
         __syncthreads();
+        // 4. fold chunk sums into the per-tree FP64 accumulators in chunk order
+        if (!OUT) {
+          for (int i = r0 * O + tid; i < r1 * O; i += NW * 32) {
+            const int t = i / O, oo = i - (i / O) * O;
+            double acc = tacc[i];
+            for (int ch = 0; ch < nch; ++ch) acc += (double)cpart[(t * cpt + ch) * O + oo];
+            tacc[i] = acc;
+          }
+          __syncthreads();
+        }
       }
+      r0 = r1;
     }
     if (!OUT) {
       for (int i = tid; i < nt * O; i += NW * 32) {
