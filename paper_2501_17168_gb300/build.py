@@ -51,10 +51,11 @@ def _stale(target, deps):
 
 
 def generate(force: bool = False):
-    """Regenerates the inline-PTX interpreter headers when their generator changed."""
+    """Regenerates the inline-PTX interpreter headers (and the forward
+    instruction-set header) when their generator changed."""
     gen = os.path.join(CSRC, "gen_interp.py")
     gen_b = os.path.join(CSRC, "gen_interp_bwd.py")
-    if force or _stale(os.path.join(CSRC, "interp_fwd.cuh"), [gen]):
+    if force or any(_stale(os.path.join(CSRC, f), [gen]) for f in ("interp_fwd.cuh", "isa_fwd.cuh")):
         subprocess.check_call([sys.executable, gen], cwd=CSRC)
     if force or _stale(os.path.join(CSRC, "interp_bwd.cuh"), [gen, gen_b]):
         subprocess.check_call([sys.executable, gen_b], cwd=CSRC)
