@@ -188,7 +188,10 @@ tgp_status tgp_batch_fitness_mse(const tgp_problem* probs, int32_t n, void* ws, 
  *              dL/dX is ADDED to it (zero it first), so calls accumulate.
  * Derivative conventions: max sends the gradient to the operand fmax
  * returned (the left one on a tie); the guard branches of pdiv and plog and
- * the clamp of cexp have zero derivative.  Intermediate values are recomputed
+ * the clamp of cexp have zero derivative.  n_features is bounded by the
+ * shared memory that holds one 128-point tile of X and of its gradient
+ * (about 175 features for trees of up to 127 nodes, 164 for 255, 95 for
+ * 1024); beyond it the call returns TGP_ERR_UNSUPPORTED.  Intermediate values are recomputed
  * per point tile (a per-thread tape of at most one value per node), never
  * stored per population x length x points.  Sums of gradients use atomic
  * additions, so their last bits may differ between runs. */

@@ -83,13 +83,13 @@ inline size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
 int pcap_of(int max_len) { return (max_len + 2 + 1) & ~1; }
 
-// Launch shape: the caller's config where given, else the heuristic.
-bool choose_shape(long long P, long long D, int F, int O, int max_len, const tgp_config* cfg,
-                  bool modi, bool mse, const DevInfo& dv, Shape* sh) {
+// Launch shape for K points per lane: the caller's config where given, else
+// the heuristic.
+bool shape_for_k(int K, long long P, long long D, int F, int O, int max_len, const tgp_config* cfg,
+                 bool modi, bool mse, const DevInfo& dv, Shape* sh) {
   Shape s{};
   s.nw = kNW;
-  s.K = (cfg && cfg->points_per_lane) ? cfg->points_per_lane : (modi ? 4 : 8);
-  if (modi) s.K = 4;  // Modi accumulators live in shared memory: 4 points per lane
+  s.K = K;
   if (s.K != 4 && s.K != 8) return false;
   const int CH = 32 * s.K;
   const int pcap = pcap_of(max_len);
@@ -144,6 +144,19 @@ bool choose_shape(long long P, long long D, int F, int O, int max_len, const tgp
   s.n_items = (long long)s.n_blocks * s.n_groups;
   *sh = s;
   return true;
+}
+
+// Launch shape: 8 points per lane for single-output populations unless the
+// caller says otherwise or the X tile of a wide feature set does not fit,
+// then 4; Modi populations always 4 (their accumulators live in shared
+// memory).
+bool choose_shape(long long P, long long D, int F, int O, int max_len, const tgp_config* cfg,
+                  bool modi, bool mse, const DevInfo& dv, Shape* sh) {
+  if (modi) return shape_for_k(4, P, D, F, O, max_len, cfg, modi, mse, dv, sh);
+  if (cfg && cfg->points_per_lane)
+    return shape_for_k(cfg->points_per_lane, P, D, F, O, max_len, cfg, modi, mse, dv, sh);
+  return shape_for_k(8, P, D, F, O, max_len, cfg, modi, mse, dv, sh) ||
+         shape_for_k(4, P, D, F, O, max_len, cfg, modi, mse, dv, sh);
 }
 
 WsLayout ws_layout(long long P, int max_len, int O, int n_groups) {

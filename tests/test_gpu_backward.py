@@ -227,3 +227,16 @@ def test_zero_upstream_tree_that_overflows_leaves_grad_X_finite(orc):
     np.testing.assert_allclose(gx, rgx, rtol=1e-3, atol=1e-3)
     np.testing.assert_allclose(gv[1], rgv[1], rtol=1e-3, atol=1e-3)
     assert (gv[0] == 0).all()
+
+
+def test_backward_feature_limit_is_reported():
+    # the adjoint holds a tile of X and of its gradient in shared memory: 256
+    # features do not fit, and the call says so instead of launching
+    p = W.random_population(96, 10, 63, n_features=256)
+    t, v, s = api.population_to(p, DEV)
+    X = torch.zeros((300, 256), device=DEV)
+    y = torch.zeros((300, 1), device=DEV)
+    g = torch.ones((10, 1), dtype=torch.float64)
+    with pytest.raises(_lib.TGPError) as e:
+        api.tgp_eval_backward(t, v, s, X, y, g, 1, max_len=p.max_len)
+    assert e.value.code == _lib.TGP_ERR_UNSUPPORTED

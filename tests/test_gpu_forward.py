@@ -287,3 +287,16 @@ def test_repeatable_bitwise():
     a, _ = gpu_mse(prob.pop, prob.X, y)
     b, _ = gpu_mse(prob.pop, prob.X, y)
     np.testing.assert_array_equal(a, b)
+
+
+def test_widest_feature_set(orc):
+    # 256 features: the 8-points-per-lane X tile does not fit in shared
+    # memory, the heuristic falls back to 4 points per lane
+    p = W.random_population(15, 20, 63, (1, 63), max_depth=6, n_features=256)
+    X = np.random.default_rng(13).standard_normal((700, 256)).astype(np.float32)
+    check_forward(orc, p, X, min_strict=0.85)
+    y = np.random.default_rng(14).standard_normal((700, 1)).astype(np.float32)
+    m, st = gpu_mse(p, X, y)
+    ref, allow, ost = orc.mse(p.type, p.val, p.size, X, y, rel_tol=1e-5)
+    r = compare_mse(m, ref, allow)
+    assert len(r["failed"]) == 0 and len(r["class_mismatch"]) == 0, r
