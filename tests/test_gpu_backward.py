@@ -240,3 +240,12 @@ def test_backward_feature_limit_is_reported():
     with pytest.raises(_lib.TGPError) as e:
         api.tgp_eval_backward(t, v, s, X, y, g, 1, max_len=p.max_len)
     assert e.value.code == _lib.TGP_ERR_UNSUPPORTED
+
+
+def test_backward_sixteen_outputs(orc):
+    rng = np.random.default_rng(20)
+    p = W.random_population(97, 40, 63, (5, 63), max_depth=8, n_features=2, n_outputs=16,
+                            modi=True, modi_max=20, fset=(W.ADD, W.SUB, W.MUL, W.SIN, W.COS, W.MAX))
+    X = rng.uniform(-1, 1, (400, 2)).astype(np.float32)
+    y = rng.standard_normal((400, 16)).astype(np.float32)
+    check_grads(orc, p, X, y, 16, rng, min_trees=10)

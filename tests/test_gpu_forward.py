@@ -300,3 +300,19 @@ def test_widest_feature_set(orc):
     ref, allow, ost = orc.mse(p.type, p.val, p.size, X, y, rel_tol=1e-5)
     r = compare_mse(m, ref, allow)
     assert len(r["failed"]) == 0 and len(r["class_mismatch"]) == 0, r
+
+
+def test_sixteen_outputs_and_single_point(orc):
+    # the largest number of outputs, and a data set of one point
+    p = W.random_population(16, 40, 127, (5, 127), max_depth=8, n_features=3, n_outputs=16,
+                            modi=True, modi_max=20)
+    X = np.random.default_rng(15).uniform(-1, 1, (600, 3)).astype(np.float32)
+    check_forward(orc, p, X, O=16, min_strict=0.8)
+    y = np.random.default_rng(16).standard_normal((600, 16)).astype(np.float32)
+    m, st = gpu_mse(p, X, y, O=16)
+    ref, allow, ost = orc.mse(p.type, p.val, p.size, X, y, n_outputs=16, rel_tol=1e-5)
+    r = compare_mse(m.ravel(), ref.ravel(), allow.ravel())
+    assert len(r["failed"]) == 0 and len(r["class_mismatch"]) == 0, r
+    q = W.random_population(17, 30, 63, n_features=2)
+    X1 = np.array([[0.25, -0.5]], np.float32)
+    check_forward(orc, q, X1, min_strict=0.9)
