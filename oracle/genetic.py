@@ -46,7 +46,7 @@ from . import evaluate as _evaluate
 _ARITY = {0: 0, 1: 0, 2: 1, 3: 2, 18: 1, 19: 2}
 
 # per-child status of an exchange (the library's reading, restated)
-DONE, TOO_LARGE, BAD_INDEX, BAD_TREE = 1, 0, -1, -2
+DONE, TOO_LARGE, SKIPPED, BAD_INDEX, BAD_TREE = 1, 0, 2, -1, -2
 # node choice modes
 EXPLICIT, RANDOM, HOIST = 0, 1, 2
 
@@ -100,18 +100,25 @@ def exchange(old_t, old_v, old_s, k, new_t, new_v, new_s, max_size):
 
 
 def subtree_exchange(old, donor, old_index, node, donor_index, donor_node, mode, max_size,
-                     out_ld, old_max_len=None, donor_max_len=None):
+                     out_ld, old_max_len=None, donor_max_len=None, apply_word=None,
+                     apply_below=0):
     """Exchange over a list of children.
 
     ``old`` and ``donor`` are (type, value, size) float32 arrays [P, ld];
     ``node`` / ``donor_node`` hold node positions (EXPLICIT) or 32-bit random
-    words (RANDOM, HOIST), read as unsigned.  In HOIST mode ``donor`` and
-    ``donor_index`` are ignored: the donor is the old tree itself.  Returns
+    words (RANDOM, HOIST), read as unsigned; ``donor_node`` None means 0.
+    In HOIST mode ``donor`` and ``donor_index`` are ignored: the donor is the
+    old tree itself.  Returns
     out arrays [n, out_ld] (NaN padded) and the int32 status per child.
     Children with an index out of range or a malformed length / subtree size
-    get an all-NaN row.  Steps per child, in order:
-      1. tree indices in range, else BAD_INDEX;
-      2. both lengths integers in [1, max_len], else BAD_TREE;
+    get an all-NaN row.  With ``apply_word`` given, child i takes part only
+    when ``apply_word[i] < apply_below`` (the operator's probability as a
+    threshold on a 32-bit word); the others are copies of their old tree
+    (SKIPPED).  Steps per child, in order:
+      0. old index in range, else BAD_INDEX; its length an integer in
+         [1, max_len], else BAD_TREE; not applied -> SKIPPED (a copy);
+      1. donor index in range, else BAD_INDEX;
+      2. donor length an integer in [1, max_len], else BAD_TREE;
       3. k: the position, or r mod len(T_old); out of range -> BAD_INDEX;
       4. size_old[k] an integer in [1, len(T_old) - k], else BAD_TREE;
       5. j: the position, r' mod len(T_donor), or k + r' mod size_old[k]
@@ -126,20 +133,33 @@ def subtree_exchange(old, donor, old_index, node, donor_index, donor_node, mode,
     oml = ot.shape[1] if old_max_len is None else old_max_len
     for i in range(n):
         a = int(old_index[i])
+        if not 0 <= a < ot.shape[0]:
+            status[i] = BAD_INDEX
+            continue
+        n_old = _count(os_[a, 0], oml)
+        if n_old is None:
+            status[i] = BAD_TREE
+            continue
+        if apply_word is not None and (int(apply_word[i]) & 0xFFFFFFFF) >= apply_below:
+            for arr, src in zip(out, (ot, ov, os_)):
+                arr[i, :n_old] = src[a, :n_old]
+            status[i] = SKIPPED
+            continue
         if mode == HOIST:
             dt, dv, ds, b, dml = ot, ov, os_, a, oml
         else:
             dt, dv, ds = donor
             b = int(donor_index[i])
             dml = dt.shape[1] if donor_max_len is None else donor_max_len
-        if not (0 <= a < ot.shape[0] and 0 <= b < dt.shape[0]):
+        if not 0 <= b < dt.shape[0]:
             status[i] = BAD_INDEX
             continue
-        n_old, n_don = _count(os_[a, 0], oml), _count(ds[b, 0], dml)
-        if n_old is None or n_don is None:
+        n_don = _count(ds[b, 0], dml)
+        if n_don is None:
             status[i] = BAD_TREE
             continue
-        r, r2 = int(node[i]) & 0xFFFFFFFF, int(donor_node[i]) & 0xFFFFFFFF
+        r = int(node[i]) & 0xFFFFFFFF
+        r2 = 0 if donor_node is None else int(donor_node[i]) & 0xFFFFFFFF
         k = r if mode == EXPLICIT else r % n_old
         if k >= n_old:
             status[i] = BAD_INDEX

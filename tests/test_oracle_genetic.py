@@ -190,6 +190,20 @@ def test_population_modes_and_statuses(gen, orc):
     assert list(st) == [gen.BAD_INDEX, gen.BAD_INDEX, gen.BAD_TREE, gen.BAD_TREE, gen.BAD_INDEX,
                         gen.BAD_INDEX]
     assert np.isnan(t).all() and np.isnan(z).all()
+    # operator probability: children whose word is not below the threshold are copies
+    aw = rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
+    thr = int(0.3 * 2 ** 32)
+    t, v, z, st = gen.subtree_exchange(old, don, oi, r1, di, r2, gen.RANDOM, 80, 96, apply_word=aw,
+                                       apply_below=thr)
+    t0, v0, z0, st0 = gen.subtree_exchange(old, don, oi, r1, di, r2, gen.RANDOM, 80, 96)
+    on = aw < thr
+    assert (st[~on] == gen.SKIPPED).all() and (st[on] == st0[on]).all()
+    assert _same(t[on], t0[on]) and _same(z[on], z0[on])
+    for i in np.flatnonzero(~on):
+        ta, va, sa = _row(a, oi[i])
+        L = len(ta)
+        assert _same(t[i, :L], ta) and _same(v[i, :L], va) and _same(z[i, :L], sa)
+        assert np.isnan(t[i, L:]).all()
 
 
 def _tournament_vectorised(f, words, minimize):
