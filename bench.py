@@ -59,10 +59,11 @@ def _args():
     ap.add_argument("--points", type=int, default=100_000, help="data points")
     ap.add_argument("--suite", action="store_true",
                     help="also time the other workloads (one JSON line each, after the main line)")
-    ap.add_argument("--case", default=None, choices=["adjoint", "modi", "batched"],
+    ap.add_argument("--case", default=None, choices=["adjoint", "modi", "batched", "genetic"],
                     help="time only one case for profiling: the fused forward + adjoint on the "
-                         "differentiation workload or the Modi forward (--pop/--points), or the "
-                         "8-problem uneven batch (one batched call, then one call per problem)")
+                         "differentiation workload or the Modi forward (--pop/--points), the "
+                         "8-problem uneven batch (one batched call, then one call per problem), "
+                         "or the genetic operators (crossover, selection, one generation)")
     return ap.parse_args()
 
 
@@ -546,6 +547,100 @@ def suite_lines(dev, steps):
                 opt.step()
             line["ms_per_adam_step"] = _timed(adam_step, 20, 1)
         out.append(line)
+    out.extend(genetic_lines(dev, steps))
+    return out
+
+
+def _timed_events(fn, steps, warmup, before=None):
+    """Mean device time of fn over `steps` launches, each bracketed by its own
+    CUDA events on the current stream (``before`` runs outside the events)."""
+    import torch
+    for _ in range(warmup):
+        if before:
+            before()
+        fn()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    for e0, e1 in evs:
+        if before:
+            before()
+        e0.record()
+        fn()
+        e1.record()
+    torch.cuda.synchronize()
+    return sum(e0.elapsed_time(e1) for e0, e1 in evs) / steps
+
+
+def genetic_lines(dev, steps):
+    """The genetic operators: crossover (subtree exchange) of 100,000
+    children of trees up to 512 nodes against the HBM roofline, tournament
+    selection, and one whole generation (fitness -> selection -> crossover ->
+    mutation) replayed from a CUDA graph."""
+    import torch
+    from paper_2501_17168_gb300 import _lib, api, evolve, workloads as W
+    hbm_gbs, _, peak_kind = _peaks()
+    out = []
+    g = W.genetic(0)
+    P = g.pop
+    pop = api.population_to(P, dev)
+    w = lambda a: torch.from_numpy(np.asarray(a, np.uint32).view(np.int32)).to(dev)
+    oi, di = torch.from_numpy(g.old_index).to(dev), torch.from_numpy(g.donor_index).to(dev)
+    k, j = w(g.node), w(g.donor_node)
+    res = api.tgp_subtree_exchange(pop, oi, k, donor=pop, donor_index=di, donor_node=j,
+                                   mode=_lib.PICK_RANDOM, max_size=512, out_ld=512)
+    outs, st = res
+
+    def xchg():
+        api.tgp_subtree_exchange(pop, oi, k, donor=pop, donor_index=di, donor_node=j,
+                                 mode=_lib.PICK_RANDOM, max_size=512, out_ld=512, out=outs, status=st)
+    ms = _timed_events(xchg, steps, 3)
+    child_nodes = float(outs[2][:, 0].double().sum())
+    # algorithmic bytes: each child node read once from its source (3 floats),
+    # the four index/word arrays, the full NaN-padded output rows and the status
+    nbytes = 12 * child_nodes + 16 * g.n + g.n * (12 * 512 + 4)
+    done = float((st == _lib.XCHG_DONE).sum())
+    out.append({"workload": "crossover: 100,000 children of 100,000 trees len U[1,511] "
+                            "(max size 512, {+,-,*,/,sin,cos,tan}), random nodes",
+                "ms_per_launch": ms, "children_per_s": g.n / (ms / 1e3),
+                "exchanged_fraction": done / g.n,
+                "roofline": {"bound": "hbm", "achieved": nbytes / (ms / 1e3) / 1e9,
+                             "peak": hbm_gbs, "unit": "GB/s",
+                             "frac": nbytes / (ms / 1e3) / 1e9 / hbm_gbs, "peak_kind": peak_kind,
+                             "algorithmic_bytes": nbytes}})
+    fit = torch.rand(P.pop, dtype=torch.float64, device=dev, generator=torch.Generator(dev).manual_seed(0))
+    words = w(W.random_words(0, (2 * P.pop, 20), 11))
+    win = torch.empty(2 * P.pop, dtype=torch.int32, device=dev)
+    ms = _timed_events(lambda: api.tgp_tournament_select(fit, words, True, winners=win), steps, 3)
+    out.append({"workload": "tournament selection: 200,000 tournaments of size 20 over 100,000 trees",
+                "ms_per_launch": ms, "selections_per_s": 2 * P.pop / (ms / 1e3)})
+    # one generation of 5,000 trees on the sr_scale data (100,000 points, 16 features)
+    prob = W.sr_scale(0)
+    Xd, yd = _gpu_targets(api, prob, dev)
+    g5 = W.genetic(1, pop=5000, len_range=(1, 255), n_features=16)
+    start = api.population_to(g5.pop, dev)
+    state = evolve.Generation(tuple(a.clone() for a in start), Xd, yd, api.population_to(g5.pool, dev))
+    state.step()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        state.step()
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        state.step()
+
+    def reset():  # every timed generation starts from the same population
+        for dst, src in zip(state.pop, start):
+            dst.copy_(src)
+    ms_gen = _timed_events(lambda: graph.replay(), steps, 2, before=reset)
+    reset()
+    ms_fit = _timed_events(lambda: api.tgp_fitness_mse(*state.pop, Xd, yd, 1, max_len=512), steps, 2)
+    out.append({"workload": "generation: 5,000 trees (max size 512) on sr_scale data (100,000 points, "
+                            "F=16): fitness + tournament(20) + crossover(0.9) + subtree mutation(0.1), "
+                            "one CUDA graph replay",
+                "ms_per_generation": ms_gen, "ms_fitness_alone": ms_fit,
+                "ms_selection_and_operators": ms_gen - ms_fit})
     return out
 
 
@@ -557,6 +652,10 @@ def run_case(a):
     from paper_2501_17168_gb300 import api, build, workloads as W
     build.build_all()
     dev = torch.device("cuda", 0)
+    if a.case == "genetic":
+        for line in genetic_lines(dev, a.steps):
+            print(json.dumps(line), flush=True)
+        return 0
     if a.case == "batched":
         bps = []
         for pr in W.batched_uneven(0):

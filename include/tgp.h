@@ -200,6 +200,116 @@ tgp_status tgp_eval_backward(const tgp_population* pop, const tgp_data* data, co
                              float* grad_value, float* grad_X, int32_t* tree_status, void* ws,
                              size_t ws_bytes, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Genetic operators on the same encoding (Sec. III-B "Tensorized Operations";
+ * Algorithm 1).  Random choices are made by the caller: every random number
+ * an operator uses is a 32-bit word passed in, so results are reproducible
+ * and independent of the launch shape.  These calls need no workspace.
+ * ------------------------------------------------------------------------- */
+
+/* How tgp_subtree_exchange finds the replaced node k of the old tree and the
+ * root j of the inserted subtree in the donor tree. */
+typedef enum {
+  TGP_PICK_NODES = 0,  /* node[i] = k and donor_node[i] = j are positions      */
+  TGP_PICK_RANDOM = 1, /* k = node[i] mod len(old), j = donor_node[i] mod
+                          len(donor): one-point crossover (donor = the second
+                          parent) and subtree mutation (donor = new trees)     */
+  TGP_PICK_HOIST = 2   /* hoist mutation: the donor is the old tree itself;
+                          k = node[i] mod len, j = k + donor_node[i] mod
+                          size[k], so a subtree of the subtree at k replaces it */
+} tgp_pick_mode;
+
+/* Per-child result of tgp_subtree_exchange. */
+enum {
+  TGP_XCHG_TOO_LARGE = 0,  /* the child would exceed max_size: it is the old
+                              tree unchanged (the paper's size rule)          */
+  TGP_XCHG_DONE = 1,       /* the child is exchange(T_old, k, T_new)          */
+  TGP_XCHG_SKIPPED = 2,    /* apply_word[i] >= apply_below: a copy of T_old   */
+  TGP_XCHG_BAD_INDEX = -1, /* a tree index or (TGP_PICK_NODES) a position out
+                              of range; the child row is all NaN              */
+  TGP_XCHG_BAD_TREE = -2   /* a length or subtree size that is not an integer
+                              within its tree; the child row is all NaN       */
+};
+
+/* Subtree exchange (Sec. III-B): child i is
+ *   T* = T_old[0..k) (+) T_new (+) T_old[k + size_old[k] .. len_old)
+ * for all three tensors, where T_new is the subtree of the donor rooted at j
+ * and every ancestor of k in the prefix has its subtree size grown by
+ * dn = size_donor[j] - size_old[k].  A child longer than max_size is the old
+ * tree unchanged.
+ *   old          population the children start from ([device] rows)
+ *   donor        population the inserted subtrees come from; ignored (may be
+ *                NULL) with TGP_PICK_HOIST
+ *   old_index    [device] int32 [n]: row of `old` for child i
+ *   node         [device] uint32 [n]: position or random word for k
+ *   donor_index  [device] int32 [n]: row of `donor` (ignored with HOIST)
+ *   donor_node   [device] uint32 [n] or NULL (= 0): position or random word
+ *                for j
+ *   apply_word   [device] uint32 [n] or NULL: child i takes part only when
+ *                apply_word[i] < apply_below (the operator's probability p as
+ *                the threshold p * 2^32); the others are copies of T_old
+ *   max_size     the maximum tree size, 1..TGP_MAX_LEN
+ *   out_type, out_value, out_size
+ *                [device] float [n, out_ld] each: the children, NaN-padded over
+ *                the whole row; out_ld >= max(max_size, old->max_len).  They
+ *                must not overlap the inputs (checked on the host).
+ *   xchg_status  [device] int32 [n] or NULL: TGP_XCHG_* per child.
+ * The exchange assumes trees that pass tgp_validate; other trees are never
+ * read outside their rows, and the checks listed for TGP_XCHG_BAD_TREE are
+ * the only ones made.  Bit-exact: each output element is a copy of an input
+ * element, or a subtree size plus dn (exact in float). */
+tgp_status tgp_subtree_exchange(const tgp_population* old, const tgp_population* donor,
+                                const int32_t* old_index, const uint32_t* node,
+                                const int32_t* donor_index, const uint32_t* donor_node,
+                                const uint32_t* apply_word, uint32_t apply_below, int64_t n,
+                                int32_t mode, int32_t max_size, float* out_type, float* out_value,
+                                float* out_size, int64_t out_ld, int32_t* xchg_status,
+                                void* stream);
+
+/* Tournament selection (Algorithm 1, "Select parents"; the tournament size is
+ * a parameter of the table "Configuration of Genetic Programming"):
+ * contestant m of selection i is tree words[i * tournament_size + m] mod pop;
+ * winners[i] is the contestant with the lowest (minimize != 0) or highest
+ * fitness; ties go to the earliest contestant and NaN loses to every number.
+ *   fitness  [device] double, tree p at fitness[p * stride] (stride >= 1, so a
+ *            column of an MSE matrix [pop, n_outputs] can be used directly)
+ *   words    [device] uint32 [n, tournament_size], tournament_size 1..4096
+ *   winners  [device] int32 [n]
+ * pop must be in [1, 2^31).  Bit-exact. */
+tgp_status tgp_tournament_select(const double* fitness, int64_t stride, int64_t pop,
+                                 const uint32_t* words, int64_t n, int32_t tournament_size,
+                                 int32_t minimize, int32_t* winners, void* stream);
+
+/* Classification fitness (Sec. V-D, measured by accuracy) from forward
+ * outputs: the predicted class of point d is the first index k of the largest
+ * non-NaN out[p, k, d] (no prediction when all are NaN), and correct[p] counts
+ * the points whose prediction equals labels[d].
+ *   out       [device] float [pop, n_classes, n_points] (tgp_eval_forward's
+ *             layout), n_classes 1..TGP_MAX_OUTPUTS, n_points >= 1
+ *   labels    [device] int32 [n_points]
+ *   correct   [device] int64 [pop] (overwritten)
+ *   accuracy  [device] double [pop] or NULL: correct / n_points
+ * Bit-exact (integer counts). */
+tgp_status tgp_accuracy_from_outputs(const float* out, int64_t pop, int32_t n_classes,
+                                     int64_t n_points, const int32_t* labels, int64_t* correct,
+                                     double* accuracy, void* stream);
+
+/* Workspace bytes of tgp_fitness_accuracy (0 on invalid arguments). */
+size_t tgp_accuracy_workspace_size(const tgp_population* pop, const tgp_data* data,
+                                   int32_t n_classes);
+
+/* Classification accuracy of every tree: the outputs of Modi nodes tagged
+ * 0..n_classes-1 (Sec. IV-C) are the class scores, evaluated by the forward
+ * kernels over chunks of points (a [pop, n_classes, chunk] buffer of at most
+ * 256 MiB, or 256 points, inside ws) and reduced as in
+ * tgp_accuracy_from_outputs.  accuracy [device] double [pop] (NaN for trees
+ * that fail validation), correct [device] int64 [pop] or NULL, tree_status
+ * [device] int32 [pop] or NULL. */
+tgp_status tgp_fitness_accuracy(const tgp_population* pop, const tgp_data* data,
+                                const int32_t* labels, int32_t n_classes, double* accuracy,
+                                int64_t* correct, int32_t* tree_status, void* ws, size_t ws_bytes,
+                                void* stream);
+
 /* Largest scratch tgp_fitness_mse_noalloc can use (32 MiB). */
 #define TGP_NOALLOC_WS_BYTES (32u << 20)
 

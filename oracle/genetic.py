@@ -3,8 +3,9 @@
 TEST INFRASTRUCTURE ONLY.  Like the rest of ``oracle/``, this module is the
 independent reference the CUDA library is checked against; only the tests,
 the smoke check and the CPU-baseline leg of the benchmark import it.  It
-shares no code with the CUDA path and works on one tree at a time with
-Python lists and numpy slices, in the order the paper states the steps.
+shares no code with the CUDA path.  The operators work on one tree (one
+selection) at a time with numpy slices, in the order the paper states the
+steps; the accuracy is plain numpy over the whole output array.
 
 What it computes:
 
@@ -27,7 +28,7 @@ What it computes:
   contestant ``m`` of selection ``i`` is tree ``r[i, m] mod P``; the winner has
   the best fitness, ties going to the earliest contestant, NaN losing to every
   number.
-* ``accuracy_from_outputs`` / ``accuracy`` -- classification fitness
+* ``predict`` / ``accuracy_from_outputs`` / ``accuracy`` -- classification fitness
   (Sec. V-D classification tasks, measured by accuracy): the predicted class
   of a point is the first index of the largest non-NaN output; accuracy is
   the fraction of points whose prediction equals the label.
@@ -206,49 +207,43 @@ def tournament(fitness, words, minimize=True):
     return win
 
 
-def _predict(o):
-    """First index of the largest non-NaN value; -1 when all are NaN."""
-    pred, best = -1, None
-    for k, v in enumerate(o):
-        if np.isnan(v):
-            continue
-        if pred < 0 or v > best:
-            pred, best = k, v
-    return pred
+def predict(out):
+    """Predicted class [P, D] of outputs [P, C, D]: the first index whose
+    output equals the largest non-NaN output of the point; -1 when all of
+    the point's outputs are NaN."""
+    out = np.asarray(out)
+    allnan = np.isnan(out).all(axis=1)
+    with np.errstate(invalid="ignore"):
+        best = np.max(np.where(np.isnan(out), -np.inf, out), axis=1)
+    first = np.argmax(out == best[:, None, :], axis=1)
+    return np.where(allnan, -1, first)
 
 
 def accuracy_from_outputs(out, labels):
     """Accuracy [P] (float64) and correct counts [P] of outputs [P, C, D]."""
-    out = np.asarray(out)
-    P, C, D = out.shape
-    lab = np.asarray(labels)
-    cnt = np.zeros(P, np.int64)
-    for p in range(P):
-        for d in range(D):
-            pr = _predict(out[p, :, d])
-            cnt[p] += int(pr >= 0 and pr == lab[d])
-    with np.errstate(invalid="ignore"):
-        acc = cnt / np.float64(D) if D else np.full(P, np.nan)
+    pred = predict(out)
+    lab = np.asarray(labels)[None, :]
+    cnt = ((pred >= 0) & (pred == lab)).sum(axis=1).astype(np.int64)
+    D = pred.shape[1]
+    acc = cnt / np.float64(D) if D else np.full(pred.shape[0], np.nan)
     return acc, cnt
 
 
 def accuracy(type_, val, size, X, labels, n_classes, max_len=None):
     """Accuracy from the FP64 forward outputs, plus per tree the number of
-    points whose prediction an FP32 evaluation could change (the largest
-    output lies within the summed error bounds of another one, or a bound is
-    not finite)."""
+    points whose prediction an FP32 evaluation could change: the predicted
+    output lies within the summed error bounds of another output, a bound or
+    an output is not finite, or there is no prediction."""
     out, err, st = _evaluate(type_, val, size, X, n_classes, with_err=True, max_len=max_len)
     acc, cnt = accuracy_from_outputs(out, labels)
-    P, C, D = out.shape
-    amb = np.zeros(P, np.int64)
-    for p in range(P):
-        for d in range(D):
-            o, e = out[p, :, d], err[p, :, d]
-            pr = _predict(o)
-            if pr < 0 or not np.all(np.isfinite(e)) or not np.all(np.isfinite(o)):
-                amb[p] += 1
-                continue
-            close = [k for k in range(C) if k != pr and o[pr] - o[k] <= e[pr] + e[k]]
-            amb[p] += int(bool(close))
+    pred = predict(out)
+    pk = np.maximum(pred, 0)[:, None, :]
+    o_p = np.take_along_axis(out, pk, axis=1)
+    e_p = np.take_along_axis(err, pk, axis=1)
+    with np.errstate(invalid="ignore"):
+        close = (o_p - out <= e_p + err)
+    close &= np.arange(n_classes)[None, :, None] != pk
+    bad = (pred < 0) | ~np.isfinite(err).all(axis=1) | ~np.isfinite(out).all(axis=1)
+    amb = (close.any(axis=1) | bad).sum(axis=1).astype(np.int64)
     acc[st != 0] = np.nan
     return acc, cnt, amb, st

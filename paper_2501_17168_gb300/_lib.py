@@ -20,6 +20,8 @@ TREE_LEN, TREE_TYPE, TREE_FUNC, TREE_VAR, TREE_MODI, TREE_CONST, TREE_SIZE, TREE
     1, 2, 4, 8, 16, 32, 64, 128
 MAX_LEN, MAX_OUTPUTS, MAX_FEATURES = 1024, 16, 256
 NOALLOC_WS_BYTES = 32 << 20
+PICK_NODES, PICK_RANDOM, PICK_HOIST = 0, 1, 2
+XCHG_TOO_LARGE, XCHG_DONE, XCHG_SKIPPED, XCHG_BAD_INDEX, XCHG_BAD_TREE = 0, 1, 2, -1, -2
 
 
 class tgp_population(ctypes.Structure):
@@ -80,6 +82,24 @@ _SIGS = {
     "tgp_fitness_mse_noalloc": (ctypes.c_int, [_P(tgp_population), _P(tgp_data), ctypes.c_void_p,
                                                ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_void_p]),
+    "tgp_subtree_exchange": (ctypes.c_int, [_P(tgp_population), _P(tgp_population),
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
+                                            ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
+    "tgp_tournament_select": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                             ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                             ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "tgp_accuracy_from_outputs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                                 ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_void_p]),
+    "tgp_accuracy_workspace_size": (ctypes.c_size_t, [_P(tgp_population), _P(tgp_data),
+                                                      ctypes.c_int32]),
+    "tgp_fitness_accuracy": (ctypes.c_int, [_P(tgp_population), _P(tgp_data), ctypes.c_void_p,
+                                            ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                            ctypes.c_void_p]),
     "tgp_check_device_error": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "tgp_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "tgp_version": (ctypes.c_char_p, []),

@@ -258,3 +258,108 @@ def tgp_batch_fitness_mse(problems, ws=None):
     check(lib.tgp_batch_fitness_mse(arr, len(problems), ws.data_ptr(), ws.numel(), _stream_handle(dev)),
           "tgp_batch_fitness_mse")
     return [p.mse for p in problems]
+
+
+# ------------------------------------------------------ genetic operators
+def _i32(t, name, n=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.int32:
+        raise TypeError(f"{name} must be a CUDA int32 tensor")
+    if not t.is_contiguous() or (n is not None and t.numel() != n):
+        raise ValueError(f"{name} must be contiguous with {n} elements")
+    return t
+
+
+def tgp_subtree_exchange(old, old_index, node, donor=None, donor_index=None, donor_node=None,
+                         mode: int = _lib.PICK_RANDOM, max_size: int = 512, out_ld=None,
+                         apply_word=None, apply_below: int = 0, old_max_len=None,
+                         donor_max_len=None, out=None, status=None):
+    """Subtree exchange (Sec. III-B) of ``len(old_index)`` children.
+
+    ``old`` / ``donor`` are (type, value, size) tuples of float32 [P, ld]
+    device tensors; ``old_index`` / ``donor_index`` int32 rows; ``node`` /
+    ``donor_node`` / ``apply_word`` int32 tensors read as uint32 words.
+    Returns ((type, value, size) of the children [n, out_ld], status int32 [n]).
+    """
+    lib = _lib.load()
+    n = old_index.numel()
+    op = make_population(*old, old_max_len)
+    dp = make_population(*donor, donor_max_len) if donor is not None else None
+    dev = old[0].device
+    _i32(old_index, "old_index", n)
+    _i32(node, "node", n)
+    if mode != _lib.PICK_HOIST:
+        if dp is None or donor_index is None:
+            raise ValueError("crossover and subtree mutation need a donor population and rows")
+        _i32(donor_index, "donor_index", n)
+    for t, name in ((donor_node, "donor_node"), (apply_word, "apply_word")):
+        if t is not None:
+            _i32(t, name, n)
+    ld = int(out_ld if out_ld is not None else max(max_size, op.max_len))
+    if out is None:
+        out = tuple(torch.empty((n, ld), dtype=torch.float32, device=dev) for _ in range(3))
+    if status is None:
+        status = torch.empty(n, dtype=torch.int32, device=dev)
+    ptr = lambda t: t.data_ptr() if t is not None else None
+    check(lib.tgp_subtree_exchange(ctypes.byref(op), _cref(dp), old_index.data_ptr(),
+                                   node.data_ptr(), ptr(donor_index), ptr(donor_node),
+                                   ptr(apply_word), int(apply_below) & 0xFFFFFFFF, n, int(mode),
+                                   int(max_size), out[0].data_ptr(), out[1].data_ptr(),
+                                   out[2].data_ptr(), ld, status.data_ptr(), _stream_handle(dev)),
+          "tgp_subtree_exchange")
+    return out, status
+
+
+def tgp_tournament_select(fitness, words, minimize: bool = True, winners=None):
+    """Winner row per selection; ``fitness`` float64 [P] (or a column view
+    with a stride), ``words`` int32 [n, t] read as uint32."""
+    lib = _lib.load()
+    if fitness.dtype != torch.float64 or not fitness.is_cuda or fitness.dim() != 1:
+        raise TypeError("fitness must be a 1-D CUDA float64 tensor")
+    if words.dim() != 2:
+        raise ValueError("words must be [n, tournament_size]")
+    _i32(words, "words")
+    n, t = words.shape
+    if winners is None:
+        winners = torch.empty(n, dtype=torch.int32, device=words.device)
+    check(lib.tgp_tournament_select(fitness.data_ptr(), max(fitness.stride(0), 1), fitness.numel(),
+                                    words.data_ptr(), n, t, int(bool(minimize)),
+                                    winners.data_ptr(), _stream_handle(words.device)),
+          "tgp_tournament_select")
+    return winners
+
+
+def tgp_accuracy_from_outputs(out, labels):
+    """(accuracy float64 [P], correct int64 [P]) of forward outputs [P, C, D]."""
+    lib = _lib.load()
+    _f32(out, "out")
+    if out.dim() != 3 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous [pop, n_classes, n_points] tensor")
+    P, C, D = out.shape
+    _i32(labels, "labels", D)
+    acc = torch.empty(P, dtype=torch.float64, device=out.device)
+    cnt = torch.empty(P, dtype=torch.int64, device=out.device)
+    check(lib.tgp_accuracy_from_outputs(out.data_ptr(), P, C, D, labels.data_ptr(), cnt.data_ptr(),
+                                        acc.data_ptr(), _stream_handle(out.device)),
+          "tgp_accuracy_from_outputs")
+    return acc, cnt
+
+
+def tgp_fitness_accuracy(type_, val, size, X, labels, n_classes: int, max_len=None):
+    """(accuracy float64 [P], correct int64 [P], tree status int32 [P])."""
+    lib = _lib.load()
+    pop = make_population(type_, val, size, max_len)
+    data = make_data(X)
+    _i32(labels, "labels", data.n_points)
+    dev = X.device
+    n = lib.tgp_accuracy_workspace_size(ctypes.byref(pop), ctypes.byref(data), n_classes)
+    if n == 0:
+        raise _lib.TGPError(_lib.TGP_ERR_INVALID_ARG, "tgp_accuracy_workspace_size")
+    ws = workspace(n, dev)
+    acc = torch.empty(pop.pop, dtype=torch.float64, device=dev)
+    cnt = torch.empty(pop.pop, dtype=torch.int64, device=dev)
+    st = torch.empty(pop.pop, dtype=torch.int32, device=dev)
+    check(lib.tgp_fitness_accuracy(ctypes.byref(pop), ctypes.byref(data), labels.data_ptr(),
+                                   n_classes, acc.data_ptr(), cnt.data_ptr(), st.data_ptr(),
+                                   ws.data_ptr(), ws.numel(), _stream_handle(dev)),
+          "tgp_fitness_accuracy")
+    return acc, cnt, st

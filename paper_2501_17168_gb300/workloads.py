@@ -274,6 +274,74 @@ def batched_uneven(seed: int = 0, n_problems: int = 8, pop_range=(1000, 20000),
     return probs
 
 
+# ------------------------------------------------- genetic-operator inputs
+def random_words(seed: int, shape, *key: int) -> np.ndarray:
+    """Uniform 32-bit words (the random numbers the operators consume)."""
+    return _rng(seed, 7, *key).integers(0, 2 ** 32, shape, dtype=np.uint64).astype(np.uint32)
+
+
+@dataclass
+class GeneticInputs:
+    """A population, a pool of new subtrees and the random words of one round
+    of crossover / mutation / selection over ``n`` children."""
+    pop: Population
+    pool: Population
+    n: int
+    old_index: np.ndarray    # int32 [n]
+    donor_index: np.ndarray  # int32 [n]
+    pool_index: np.ndarray   # int32 [n]
+    node: np.ndarray         # uint32 [n]
+    donor_node: np.ndarray   # uint32 [n]
+    apply: np.ndarray        # uint32 [n]
+
+
+def genetic(seed: int = 0, pop: int = 100_000, max_size: int = 512, len_range=(1, 511),
+            n: int | None = None, pool: int = 4096, pool_len=(1, 31), n_features: int = 16,
+            fset=PAPER_FSET) -> GeneticInputs:
+    """Trees of the paper's SR setting (maximum tree size 512, function set
+    {+,-,*,/,sin,cos,tan}) with lengths uniform on ``len_range``, a pool of
+    small random trees for subtree mutation, uniform parent rows and words."""
+    n = pop if n is None else n
+    p = random_population(_seed64(seed, 8), pop, max_size, len_range, max_depth=20, fset=fset,
+                          n_features=n_features)
+    q = random_population(_seed64(seed, 9), pool, pool_len[1], pool_len, max_depth=8, fset=fset,
+                          n_features=n_features, ld=pool_len[1])
+    r = _rng(seed, 8, 1)
+    rows = lambda m: r.integers(0, m, n).astype(np.int32)
+    return GeneticInputs(p, q, n, rows(pop), rows(pop), rows(pool), random_words(seed, n, 1),
+                         random_words(seed, n, 2), random_words(seed, n, 3))
+
+
+#: (features, classes, points) of the paper's classification data sets
+#: (table "Details of Classification Datasets")
+CLASSIFICATION_SHAPES = {"wine": (13, 3, 178), "kidney": (24, 3, 400), "breast": (30, 2, 569),
+                         "yeast": (8, 10, 1484)}
+
+
+@dataclass
+class ClassProblem:
+    name: str
+    pop: Population
+    X: np.ndarray       # [D, F] float32
+    labels: np.ndarray  # [D] int32
+    n_classes: int
+
+
+def classification(seed: int = 0, shape: str = "yeast", pop: int = 5000, max_len: int = 255,
+                   D: int | None = None) -> ClassProblem:
+    """Modi trees with one output per class (Sec. IV-C) on a synthetic data
+    set of the named shape: X ~ N(0, 1), labels uniform over the classes."""
+    F, C, D0 = CLASSIFICATION_SHAPES[shape]
+    D = D0 if D is None else D
+    key = sorted(CLASSIFICATION_SHAPES).index(shape)
+    p = random_population(_seed64(seed, 10, key), pop, max_len, (1, max_len), max_depth=10,
+                          fset=SR_FSET, n_features=F, n_outputs=C, modi=True, modi_max=16)
+    r = _rng(seed, 10, key)
+    X = r.standard_normal((D, F), dtype=np.float32)
+    labels = r.integers(0, C, D).astype(np.int32)
+    return ClassProblem(shape, p, X, labels, C)
+
+
 WORKLOADS = {
     "sr_small": sr_small,
     "sr_scale": sr_scale,

@@ -60,3 +60,41 @@ def test_host_argument_checks_need_no_device(lib):
     pop = _lib.tgp_population(None, None, None, 0, 8, 8)
     assert lib.tgp_validate(ctypes.byref(pop), 0, 1, None, None, 0, None) == _lib.TGP_ERR_INVALID_ARG
     assert lib.tgp_validate(ctypes.byref(pop), 1, 99, None, None, 0, None) == _lib.TGP_ERR_INVALID_ARG
+
+
+def test_genetic_operator_argument_checks_need_no_device(lib):
+    u32 = ctypes.c_uint32
+    old = _lib.tgp_population(0x10000, 0x20000, 0x30000, 4, 8, 8)   # fake, never dereferenced
+    idx, words = ctypes.c_void_p(0x40000), ctypes.c_void_p(0x50000)
+    outs = [ctypes.c_void_p(0x60000), ctypes.c_void_p(0x70000), ctypes.c_void_p(0x80000)]
+
+    def xchg(mode=_lib.PICK_RANDOM, n=2, max_size=8, out_ld=8, o=outs, donor=old):
+        return lib.tgp_subtree_exchange(ctypes.byref(old), ctypes.byref(donor), idx, words, idx,
+                                        words, None, u32(0), n, mode, max_size, *o, out_ld, None,
+                                        None)
+
+    assert xchg(mode=7) == _lib.TGP_ERR_INVALID_ARG
+    assert xchg(max_size=0) == _lib.TGP_ERR_INVALID_ARG
+    assert xchg(max_size=2000, out_ld=2000) == _lib.TGP_ERR_INVALID_ARG   # beyond TGP_MAX_LEN
+    assert xchg(max_size=16, out_ld=8) == _lib.TGP_ERR_INVALID_ARG        # row narrower than the limit
+    assert xchg(max_size=4, out_ld=4) == _lib.TGP_ERR_INVALID_ARG         # narrower than old rows
+    assert xchg(n=0) == _lib.TGP_OK
+    assert xchg(n=-1) == _lib.TGP_ERR_INVALID_ARG
+    clash = [ctypes.c_void_p(0x10040), outs[1], outs[2]]                 # inside old.type
+    assert xchg(o=clash) == _lib.TGP_ERR_INVALID_ARG
+    same = [outs[0], outs[0], outs[2]]
+    assert xchg(o=same) == _lib.TGP_ERR_INVALID_ARG
+    nulls = [None, outs[1], outs[2]]
+    assert xchg(o=nulls) == _lib.TGP_ERR_INVALID_ARG
+    fit = ctypes.c_void_p(0x90000)
+    assert lib.tgp_tournament_select(fit, 1, 10, words, 4, 0, 1, idx, None) == _lib.TGP_ERR_INVALID_ARG
+    assert lib.tgp_tournament_select(fit, 1, 0, words, 4, 3, 1, idx, None) == _lib.TGP_ERR_INVALID_ARG
+    assert lib.tgp_tournament_select(fit, 0, 10, words, 4, 3, 1, idx, None) == _lib.TGP_ERR_INVALID_ARG
+    assert lib.tgp_tournament_select(fit, 1, 10, words, 0, 3, 1, idx, None) == _lib.TGP_OK
+    assert lib.tgp_accuracy_from_outputs(fit, 4, 0, 10, idx, idx, None, None) == _lib.TGP_ERR_INVALID_ARG
+    assert lib.tgp_accuracy_from_outputs(fit, 4, 3, 0, idx, idx, None, None) == _lib.TGP_ERR_INVALID_ARG
+    assert lib.tgp_accuracy_from_outputs(fit, 0, 3, 10, idx, idx, None, None) == _lib.TGP_OK
+    data = _lib.tgp_data(0xA0000, 0, 2, 2)
+    assert lib.tgp_accuracy_workspace_size(ctypes.byref(old), ctypes.byref(data), 3) == 0
+    assert lib.tgp_fitness_accuracy(ctypes.byref(old), ctypes.byref(data), idx, 3, idx, None, None,
+                                    None, 0, None) == _lib.TGP_ERR_INVALID_ARG

@@ -250,20 +250,32 @@ def test_tournament_best_tree_probability(gen):
     assert (gen.tournament(f, sub) == win[:2000]).all()
 
 
-def test_accuracy_from_outputs_against_argmax(gen):
+def _predict_loop(o):
+    """First index of the largest non-NaN value, scanning once; -1 if none."""
+    pred, best = -1, None
+    for k, v in enumerate(o):
+        if v != v:
+            continue
+        if pred < 0 or v > best:
+            pred, best = k, v
+    return pred
+
+
+def test_accuracy_from_outputs_against_scan(gen):
     rng = np.random.default_rng(6)
     P, C, D = 6, 5, 300
     out = rng.integers(-2, 3, (P, C, D)).astype(np.float32)      # many ties
     out[rng.random((P, C, D)) < 0.15] = np.nan
-    out[0, :, :10] = np.nan                                      # rows with no prediction
+    out[rng.random((P, C, D)) < 0.05] = -np.inf
+    out[0, :, :10] = np.nan                                      # points with no prediction
+    out[1, :, :10] = -np.inf                                     # all -inf: class 0
+    out[2, 0, :10], out[2, 1:, :10] = np.nan, -np.inf            # NaN then -inf: class 1
     lab = rng.integers(0, C, D).astype(np.int32)
     acc, cnt = gen.accuracy_from_outputs(out, lab)
-    filled = np.where(np.isnan(out), -np.inf, out)
-    pred = np.argmax(filled, axis=1)                             # first maximum
-    allnan = np.isnan(out).all(axis=1)
-    # argmax over -inf fill picks index 0 for an all -inf row; those have no prediction
-    want = ((pred == lab[None, :]) & ~allnan).sum(1)
-    # a row whose only finite values are -inf is not produced above
+    pred = np.array([[_predict_loop(out[p, :, d]) for d in range(D)] for p in range(P)])
+    assert (pred[1, :10] == 0).all() and (pred[2, :10] == 1).all() and (pred[0, :10] == -1).all()
+    assert (gen.predict(out) == pred).all()
+    want = ((pred >= 0) & (pred == lab[None, :])).sum(1)
     assert (cnt == want).all()
     np.testing.assert_array_equal(acc, want / D)
 
