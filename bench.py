@@ -636,6 +636,17 @@ def genetic_lines(dev, steps):
     ms_gen = _timed_events(lambda: graph.replay(), steps, 2, before=reset)
     reset()
     ms_fit = _timed_events(lambda: api.tgp_fitness_mse(*state.pop, Xd, yd, 1, max_len=512), steps, 2)
+    # classification: 5,000 Modi trees (one output per class) on yeast-shaped data
+    cp = W.classification(0, "yeast", pop=5000)
+    ct, cv, cs = api.population_to(cp.pop, dev)
+    cX = torch.from_numpy(cp.X).to(dev)
+    clab = torch.from_numpy(cp.labels).to(dev)
+    ms_acc = _timed_events(lambda: api.tgp_fitness_accuracy(ct, cv, cs, cX, clab, cp.n_classes,
+                                                            max_len=cp.pop.max_len), steps, 2)
+    out.append({"workload": "classification: 5,000 Modi trees len<=255 on yeast-shaped data "
+                            "(1,484 points, 8 features, 10 classes): accuracy of every tree",
+                "ms_per_call": ms_acc,
+                "node_points_per_s": cp.pop.nodes() * cp.X.shape[0] / (ms_acc / 1e3)})
     out.append({"workload": "generation: 5,000 trees (max size 512) on sr_scale data (100,000 points, "
                             "F=16): fitness + tournament(20) + crossover(0.9) + subtree mutation(0.1), "
                             "one CUDA graph replay",
