@@ -59,11 +59,13 @@ def _args():
     ap.add_argument("--points", type=int, default=100_000, help="data points")
     ap.add_argument("--suite", action="store_true",
                     help="also time the other workloads (one JSON line each, after the main line)")
-    ap.add_argument("--case", default=None, choices=["adjoint", "modi", "batched", "genetic"],
+    ap.add_argument("--case", default=None,
+                    choices=["adjoint", "modi", "batched", "genetic", "sweep"],
                     help="time only one case for profiling: the fused forward + adjoint on the "
                          "differentiation workload or the Modi forward (--pop/--points), the "
                          "8-problem uneven batch (one batched call, then one call per problem), "
-                         "or the genetic operators (crossover, selection, one generation)")
+                         "the genetic operators (crossover, selection, one generation), or the "
+                         "fitness throughput over the paper's population x data set grid")
     return ap.parse_args()
 
 
@@ -655,6 +657,32 @@ def genetic_lines(dev, steps):
     return out
 
 
+def sweep_lines(dev, steps):
+    """Fitness throughput over the grid of the paper's GPops/s summary table:
+    population sizes 100..1,000,000 x the four SR data set shapes, trees of
+    300-511 nodes.  Node-point evaluations per second of tgp_fitness_mse
+    (inputs resident, CUDA events per call)."""
+    import torch
+    from paper_2501_17168_gb300 import api, workloads as W
+    big = W.sweep_population(0, max(W.SWEEP_POPS))
+    lens = big.lengths()
+    t, v, s = api.population_to(big, dev)
+    out = []
+    for name, (D, F) in W.SR_DATASET_SHAPES.items():
+        Xn, yn = W.sweep_data(0, name)
+        X, y = torch.from_numpy(Xn).to(dev), torch.from_numpy(yn).to(dev)
+        for P in W.SWEEP_POPS:
+            fn = lambda: api.tgp_fitness_mse(t[:P], v[:P], s[:P], X, y, 1, max_len=512)
+            reps = steps if P * D <= 10 ** 9 else 2
+            ms = _timed_events(fn, reps, 1)
+            units = float(lens[:P].sum()) * D
+            out.append({"workload": f"sweep {name}: {P} trees len U[300,511] x {D} points, F={F}",
+                        "pop": P, "n_points": D, "ms_per_call": ms,
+                        "node_points_per_s": units / (ms / 1e3)})
+        del X, y
+    return out
+
+
 def run_case(a):
     """One small case for the kernel profiles: the fused forward + adjoint of
     the differentiation workload (constants and inputs), or the Modi forward
@@ -663,6 +691,10 @@ def run_case(a):
     from paper_2501_17168_gb300 import api, build, workloads as W
     build.build_all()
     dev = torch.device("cuda", 0)
+    if a.case == "sweep":
+        for line in sweep_lines(dev, a.steps):
+            print(json.dumps(line), flush=True)
+        return 0
     if a.case == "genetic":
         for line in genetic_lines(dev, a.steps):
             print(json.dumps(line), flush=True)

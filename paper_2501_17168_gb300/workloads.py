@@ -274,6 +274,31 @@ def batched_uneven(seed: int = 0, n_problems: int = 8, pop_range=(1000, 20000),
     return probs
 
 
+# ------------------------------------------------ paper-shape sweep inputs
+#: (points, features) of the paper's SR data sets (table "Details of Symbolic
+#: Regression Datasets"; Auto MPG as counted in the GPops/s summary table)
+SR_DATASET_SHAPES = {"daily_demand": (60, 12), "auto_mpg": (392, 7),
+                     "california_housing": (20_640, 8), "feynman_i_9_18": (100_000, 9)}
+#: population sizes of the GPops/s summary table
+SWEEP_POPS = (100, 500, 1000, 5000, 10_000, 50_000, 100_000, 500_000, 1_000_000)
+
+
+def sweep_population(seed: int = 0, pop: int = 1_000_000) -> Population:
+    """Trees for the paper-shape sweep: lengths U[300, 511] in rows of 512
+    (mean ~405, the scale of the paper's S-bar), the paper's function set,
+    feature indices below 7 so that every data set shape can use them."""
+    return random_population(_seed64(seed, 11), pop, 512, (300, 511), max_depth=20,
+                             fset=PAPER_FSET, n_features=7)
+
+
+def sweep_data(seed: int, name: str) -> tuple[np.ndarray, np.ndarray]:
+    """X ~ N(0, 1) and targets ~ N(0, 1) of a data set's shape."""
+    D, F = SR_DATASET_SHAPES[name]
+    r = _rng(seed, 11, sorted(SR_DATASET_SHAPES).index(name))
+    return (r.standard_normal((D, F), dtype=np.float32),
+            r.standard_normal((D, 1), dtype=np.float32))
+
+
 # ------------------------------------------------- genetic-operator inputs
 def random_words(seed: int, shape, *key: int) -> np.ndarray:
     """Uniform 32-bit words (the random numbers the operators consume)."""
