@@ -149,12 +149,17 @@ bool shape_for_k(int K, long long P, long long D, int F, int O, int max_len, con
 // Launch shape: 8 points per lane for single-output populations unless the
 // caller says otherwise or the X tile of a wide feature set does not fit,
 // then 4; Modi populations always 4 (their accumulators live in shared
-// memory).
+// memory).  A single problem of at most 128 points also takes 4: a warp's
+// 256 slots at 8 per lane would leave most lanes idle (60 points: 14%
+// faster with 4 per lane, measured).  A batch keeps 8 so that its problems
+// share one kernel variant.
 bool choose_shape(long long P, long long D, int F, int O, int max_len, const tgp_config* cfg,
-                  bool modi, bool mse, const DevInfo& dv, Shape* sh) {
+                  bool modi, bool mse, const DevInfo& dv, Shape* sh, bool single) {
   if (modi) return shape_for_k(4, P, D, F, O, max_len, cfg, modi, mse, dv, sh);
   if (cfg && cfg->points_per_lane)
     return shape_for_k(cfg->points_per_lane, P, D, F, O, max_len, cfg, modi, mse, dv, sh);
+  if (single && D <= 32 * 4 && shape_for_k(4, P, D, F, O, max_len, cfg, modi, mse, dv, sh))
+    return true;
   return shape_for_k(8, P, D, F, O, max_len, cfg, modi, mse, dv, sh) ||
          shape_for_k(4, P, D, F, O, max_len, cfg, modi, mse, dv, sh);
 }
@@ -190,12 +195,13 @@ bool data_ok(const tgp_data* d) {
 
 // Shapes of both kernel variants share n_groups so one partial buffer serves.
 bool shapes_for(const tgp_population* pop, const tgp_data* data, int O, const tgp_config* cfg,
-                bool mse, const DevInfo& dv, Shape* plain, Shape* modi) {
+                bool mse, const DevInfo& dv, Shape* plain, Shape* modi, bool single) {
   long long D = data ? data->n_points : 0;
   int F = data ? data->n_features : 1;
-  if (!choose_shape(pop->pop, D, F, O, pop->max_len, cfg, true, mse, dv, modi)) return false;
+  if (!choose_shape(pop->pop, D, F, O, pop->max_len, cfg, true, mse, dv, modi, single)) return false;
   if (O == 1) {
-    if (!choose_shape(pop->pop, D, F, O, pop->max_len, cfg, false, mse, dv, plain)) return false;
+    if (!choose_shape(pop->pop, D, F, O, pop->max_len, cfg, false, mse, dv, plain, single))
+      return false;
   } else {
     *plain = *modi;
   }
@@ -216,8 +222,8 @@ struct Planned {
   size_t base;      // offset of this problem's workspace region
 };
 
-tgp_status plan(Planned& q, const tgp_config* cfg, bool mse, const DevInfo& dv) {
-  if (!shapes_for(q.pop, q.data, q.O, cfg, mse, dv, &q.sp, &q.sm)) return TGP_ERR_UNSUPPORTED;
+tgp_status plan(Planned& q, const tgp_config* cfg, bool mse, const DevInfo& dv, bool single) {
+  if (!shapes_for(q.pop, q.data, q.O, cfg, mse, dv, &q.sp, &q.sm, single)) return TGP_ERR_UNSUPPORTED;
   const int n_groups = q.sm.n_groups > q.sp.n_groups ? q.sm.n_groups : q.sp.n_groups;
   q.w = ws_layout(q.pop->pop, q.pop->max_len, q.O, mse ? n_groups : 0);
   for (Shape* sh : {&q.sp, &q.sm}) {
@@ -422,7 +428,7 @@ tgp_status run(const tgp_population* pop, const tgp_data* data, const float* y, 
   if (!dev_info(&dv)) return TGP_ERR_CUDA;
   Planned q{pop, data, y, O, out, mse_out, tree_status};
   q.base = 0;
-  tgp_status s = plan(q, cfg, mse, dv);
+  tgp_status s = plan(q, cfg, mse, dv, true);
   if (s != TGP_OK) return s;
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < q.w.total) return TGP_ERR_WORKSPACE;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -459,7 +465,7 @@ tgp_status plan_batch(const tgp_problem* probs, int n, const DevInfo& dv, Planne
                              p.cfg.points_per_lane)
                                 ? &p.cfg
                                 : nullptr;
-    tgp_status s = plan(q, cfg, true, dv);
+    tgp_status s = plan(q, cfg, true, dv, false);
     if (s != TGP_OK) return s;
     q.base = off;
     off = al256(off + q.w.total);
@@ -503,7 +509,7 @@ tgp_status run_backward(const tgp_population* pop, const tgp_data* data, const f
   DevInfo dv;
   if (!dev_info(&dv)) return TGP_ERR_CUDA;
   Shape sp, sm;
-  if (!shapes_for(pop, data, O, nullptr, true, dv, &sp, &sm)) return TGP_ERR_UNSUPPORTED;
+  if (!shapes_for(pop, data, O, nullptr, true, dv, &sp, &sm, true)) return TGP_ERR_UNSUPPORTED;
   const int n_groups = sm.n_groups > sp.n_groups ? sm.n_groups : sp.n_groups;
   WsLayout w = ws_layout(pop->pop, pop->max_len, O, n_groups);
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < w.total) return TGP_ERR_WORKSPACE;
@@ -607,7 +613,7 @@ size_t tgp_workspace_size(const tgp_population* pop, const tgp_data* data, int32
   int n_groups = 0;
   if (data && data->n_points > 0) {
     Shape sp, sm;
-    if (!shapes_for(pop, data, n_outputs, cfg, true, dv, &sp, &sm)) return 0;
+    if (!shapes_for(pop, data, n_outputs, cfg, true, dv, &sp, &sm, true)) return 0;
     n_groups = sm.n_groups > sp.n_groups ? sm.n_groups : sp.n_groups;
   }
   return ws_layout(pop->pop, pop->max_len, n_outputs, n_groups).total;
