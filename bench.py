@@ -602,10 +602,19 @@ def genetic_lines(dev, steps):
     # the four index/word arrays, the full NaN-padded output rows and the status
     nbytes = 12 * child_nodes + 16 * g.n + g.n * (12 * 512 + 4)
     done = float((st == _lib.XCHG_DONE).sum())
+    # the oracle beside it: its one-child-at-a-time exchange on a sample
+    from oracle import genetic as ogen
+    m = 2000
+    t0 = time.perf_counter()
+    ogen.subtree_exchange((P.type, P.val, P.size), (P.type, P.val, P.size), g.old_index[:m],
+                          g.node[:m], g.donor_index[:m], g.donor_node[:m], ogen.RANDOM, 512, 512)
+    dt = time.perf_counter() - t0
     out.append({"workload": "crossover: 100,000 children of 100,000 trees len U[1,511] "
                             "(max size 512, {+,-,*,/,sin,cos,tan}), random nodes",
                 "ms_per_launch": ms, "children_per_s": g.n / (ms / 1e3),
                 "exchanged_fraction": done / g.n,
+                "cpu_baseline": {"value": m / dt, "unit": "children/s", "cores": 1, "kind": "oracle",
+                                 "sample": f"the first {m} children, {dt:.2f} s wall"},
                 "roofline": {"bound": "hbm", "achieved": nbytes / (ms / 1e3) / 1e9,
                              "peak": hbm_gbs, "unit": "GB/s",
                              "frac": nbytes / (ms / 1e3) / 1e9 / hbm_gbs, "peak_kind": peak_kind,
@@ -614,8 +623,17 @@ def genetic_lines(dev, steps):
     words = w(W.random_words(0, (2 * P.pop, 20), 11))
     win = torch.empty(2 * P.pop, dtype=torch.int32, device=dev)
     ms = _timed_events(lambda: api.tgp_tournament_select(fit, words, True, winners=win), steps, 3)
+    m = 20_000
+    fit_h = fit.cpu().numpy()
+    words_h = W.random_words(0, (2 * P.pop, 20), 11)[:m]
+    t0 = time.perf_counter()
+    ogen.tournament(fit_h, words_h)
+    dt = time.perf_counter() - t0
     out.append({"workload": "tournament selection: 200,000 tournaments of size 20 over 100,000 trees",
-                "ms_per_launch": ms, "selections_per_s": 2 * P.pop / (ms / 1e3)})
+                "ms_per_launch": ms, "selections_per_s": 2 * P.pop / (ms / 1e3),
+                "cpu_baseline": {"value": m / dt, "unit": "selections/s", "cores": 1,
+                                 "kind": "oracle",
+                                 "sample": f"the first {m} tournaments, {dt:.2f} s wall"}})
     # one generation of 5,000 trees on the sr_scale data (100,000 points, 16 features)
     prob = W.sr_scale(0)
     Xd, yd = _gpu_targets(api, prob, dev)
