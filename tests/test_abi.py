@@ -98,3 +98,21 @@ def test_genetic_operator_argument_checks_need_no_device(lib):
     assert lib.tgp_accuracy_workspace_size(ctypes.byref(old), ctypes.byref(data), 3) == 0
     assert lib.tgp_fitness_accuracy(ctypes.byref(old), ctypes.byref(data), idx, 3, idx, None, None,
                                     None, 0, None) == _lib.TGP_ERR_INVALID_ARG
+
+
+def test_header_compiles_as_c_and_a_c_client_runs(lib, tmp_path):
+    """include/tgp.h is plain C11: a C client compiles with -Wall -Werror,
+    links the library and runs its host-side checks (no GPU needed)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    exe = tmp_path / "abi_smoke"
+    build_dir = os.path.dirname(_lib.LIB_PATH)
+    cmd = ["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror", "-pedantic",
+           "-I", os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "c", "abi_smoke.c"),
+           "-o", str(exe), "-L", build_dir, "-ltgp", f"-Wl,-rpath,{build_dir}"]
+    subprocess.run(cmd, check=True, capture_output=True, text=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == "ok"
