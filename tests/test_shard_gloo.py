@@ -1,6 +1,9 @@
 """Sharding of the fitness path across ranks, checked on CPU with the gloo
-backend (world size 2): population ranges partition the trees, and
-point-sharded MSEs combined by one all-reduce equal the unsharded MSE."""
+backend (world size 2): population ranges partition the trees,
+point-sharded MSEs combined by one all-reduce equal the unsharded MSE, and a
+generation whose fitness is sharded by population (one all-gather) and whose
+selection and operators are replicated gives every rank the same children as
+one process."""
 import os
 import socket
 
@@ -57,3 +60,53 @@ def test_point_sharded_mse_equals_unsharded():
         p.join(120)
         assert p.exitcode == 0
     assert q.get(timeout=10) < 1e-12
+
+
+def _generation_worker(rank, world, port, q):
+    import oracle
+    from oracle import genetic
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    torch.distributed.init_process_group("gloo", rank=rank, world_size=world)
+    prob = W.sr_small(4)
+    pop3 = (prob.pop.type, prob.pop.val, prob.pop.size)
+    y = np.random.default_rng(1).standard_normal((prob.D, 1)).astype(np.float32)
+    a, b = shard.population_range(prob.pop.pop, rank, world)
+    m, _ = oracle.mse(*(t[a:b] for t in pop3), prob.X, y, threads=1)
+    fit = shard.gather_fitness(torch.from_numpy(m[:, 0]), prob.pop.pop).numpy()
+    P = prob.pop.pop
+    words = W.random_words(5, (2 * P, 20))
+    win = genetic.tournament(fit, words)
+    k, j = W.random_words(6, P), W.random_words(7, P)
+    kids = genetic.subtree_exchange(pop3, pop3, win[:P], k, win[P:], j, genetic.RANDOM,
+                                    prob.pop.max_len, prob.pop.max_len)
+    q.put((rank, fit, kids[0], kids[2], kids[3]))
+    torch.distributed.destroy_process_group()
+
+
+def test_population_sharded_generation_matches_one_process():
+    import oracle
+    from oracle import genetic
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_generation_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = [q.get(timeout=120) for _ in range(2)]
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    prob = W.sr_small(4)
+    pop3 = (prob.pop.type, prob.pop.val, prob.pop.size)
+    y = np.random.default_rng(1).standard_normal((prob.D, 1)).astype(np.float32)
+    m, _ = oracle.mse(*pop3, prob.X, y, threads=1)
+    P = prob.pop.pop
+    win = genetic.tournament(m[:, 0], W.random_words(5, (2 * P, 20)))
+    kids = genetic.subtree_exchange(pop3, pop3, win[:P], W.random_words(6, P), win[P:],
+                                    W.random_words(7, P), genetic.RANDOM, prob.pop.max_len,
+                                    prob.pop.max_len)
+    for rank, fit, t, s, st in got:
+        assert np.array_equal(fit, m[:, 0], equal_nan=True)
+        assert np.array_equal(t, kids[0], equal_nan=True) and np.array_equal(s, kids[2], equal_nan=True)
+        assert (st == kids[3]).all()
