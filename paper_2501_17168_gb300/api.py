@@ -297,8 +297,13 @@ def tgp_subtree_exchange(old, old_index, node, donor=None, donor_index=None, don
     ld = int(out_ld if out_ld is not None else max(max_size, op.max_len))
     if out is None:
         out = tuple(torch.empty((n, ld), dtype=torch.float32, device=dev) for _ in range(3))
+    for t in out:
+        _f32(t, "out")
+        if t.shape != (n, ld) or not t.is_contiguous():
+            raise ValueError(f"out tensors must be contiguous float32 [{n}, {ld}]")
     if status is None:
         status = torch.empty(n, dtype=torch.int32, device=dev)
+    _i32(status, "status", n)
     ptr = lambda t: t.data_ptr() if t is not None else None
     check(lib.tgp_subtree_exchange(ctypes.byref(op), _cref(dp), old_index.data_ptr(),
                                    node.data_ptr(), ptr(donor_index), ptr(donor_node),
@@ -321,6 +326,7 @@ def tgp_tournament_select(fitness, words, minimize: bool = True, winners=None):
     n, t = words.shape
     if winners is None:
         winners = torch.empty(n, dtype=torch.int32, device=words.device)
+    _i32(winners, "winners", n)
     check(lib.tgp_tournament_select(fitness.data_ptr(), max(fitness.stride(0), 1), fitness.numel(),
                                     words.data_ptr(), n, t, int(bool(minimize)),
                                     winners.data_ptr(), _stream_handle(words.device)),
