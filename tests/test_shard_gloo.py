@@ -110,3 +110,33 @@ def test_population_sharded_generation_matches_one_process():
         assert np.array_equal(fit, m[:, 0], equal_nan=True)
         assert np.array_equal(t, kids[0], equal_nan=True) and np.array_equal(s, kids[2], equal_nan=True)
         assert (st == kids[3]).all()
+
+
+def _gather_worker(rank, world, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    torch.distributed.init_process_group("gloo", rank=rank, world_size=world)
+    for P in (1, 2, 7, 64):
+        a, b = shard.population_range(P, rank, world)
+        local = torch.arange(a, b, dtype=torch.float64) * 0.5
+        full = shard.gather_fitness(local, P)
+        q.put((rank, P, full.tolist()))
+    torch.distributed.destroy_process_group()
+
+
+def test_gather_fitness_with_uneven_slices():
+    """Three ranks, populations that do not divide evenly (and one smaller
+    than the world): every rank gets the whole vector in tree order."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    world = 3
+    procs = [ctx.Process(target=_gather_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = [q.get(timeout=120) for _ in range(4 * world)]
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    for rank, P, full in got:
+        assert full == [0.5 * i for i in range(P)], (rank, P)
