@@ -44,6 +44,15 @@ L2_FLUSH_BYTES = 256 << 20
 FP32_OPS = {0: 1, 1: 1, 2: 1, 3: 2, 4: 1, 5: 1, 6: 1, 7: 2, 8: 2, 9: 2}
 SFU_CYC = {3: 1 / 16, 5: 1 / 16, 6: 1 / 16, 7: 1 / 16, 8: 1 / 32, 9: 3 / 16}
 MSE_FP32_PER_POINT = 2
+# Extra algorithmic work of the reverse sweep per function node-point: the
+# local derivatives and adjoint products (add/sub pass the adjoint through;
+# pdiv reuses the reciprocal of the forward; sin/cos need the other of the
+# pair; plog one reciprocal; tan 1 + t^2), one accumulate per constant or
+# feature leaf, and the seed 2 g (o - y) / D per point and output.
+ADJ_FP32_OPS = {0: 0, 1: 0, 2: 2, 3: 4, 4: 1, 5: 1, 6: 1, 7: 1, 8: 1, 9: 2}
+ADJ_SFU_CYC = {5: 1 / 16, 6: 1 / 16, 7: 1 / 16}
+ADJ_LEAF_FP32 = 1
+ADJ_SEED_FP32_PER_POINT = 2
 
 
 def _args():
@@ -57,6 +66,10 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--pop", type=int, default=5000, help="trees (smaller cases for profiling)")
     ap.add_argument("--points", type=int, default=100_000, help="data points")
+    ap.add_argument("--no-parts", action="store_true",
+                    help="skip the metric's other parts in the default line (forward + adjoint on "
+                         "the differentiation workload, the autotuned uneven batch, the Modi "
+                         "workload)")
     ap.add_argument("--suite", action="store_true",
                     help="also time the other workloads (one JSON line each, after the main line)")
     ap.add_argument("--case", default=None,
@@ -173,6 +186,23 @@ def _roofline_time(pop, D, sms, f_hz, hbm_gbs, n_outputs=1):
     t_fp32 = n_fp32 / (sms * 128 * f_hz)
     t_sfu = n_sfu / (sms * f_hz)
     return t_fp32, t_sfu
+
+
+def _roofline_time_fwd_bwd(pop, D, sms, f_hz, n_outputs=1):
+    """FP32-issue and SFU-issue times of one fused forward + adjoint pass."""
+    t_fp32, t_sfu = _roofline_time(pop, D, sms, f_hz, 0.0, n_outputs)
+    n_fp32, n_sfu = 0.0, 0.0
+    t, v = pop.type, pop.val
+    L = pop.lengths()
+    mask = np.arange(pop.ld)[None, :] < L[:, None]
+    fn = mask & ((t == 2) | (t == 3) | (t == 18) | (t == 19))
+    ids, counts = np.unique(np.mod(v[fn].astype(np.int64), 256), return_counts=True)
+    for f, c in zip(ids, counts):
+        n_fp32 += ADJ_FP32_OPS[int(f)] * c * D
+        n_sfu += ADJ_SFU_CYC.get(int(f), 0.0) * c * D
+    n_leaf = int((mask & ((t == 0) | (t == 1))).sum())
+    n_fp32 += ADJ_LEAF_FP32 * n_leaf * D + ADJ_SEED_FP32_PER_POINT * pop.pop * n_outputs * D
+    return t_fp32 + n_fp32 / (sms * 128 * f_hz), t_sfu + n_sfu / (sms * f_hz)
 
 
 def _bytes_once(pop, D, F, n_outputs=1):
@@ -332,9 +362,228 @@ def run_ours(a, rank, world, local_rank):
         }
         if not a.no_e2e:
             result["e2e"] = e2e(prob, dev, a, units)
+        if not a.no_parts and world == 1:
+            # the metric's other parts: fwd+bwd time, the batched schedule
+            # against one launch per problem, and the multi-output workload
+            peaks = (hbm_gbs, sm_max_mhz, peak_kind, sms)
+            del flush
+            for name, fn in (("fwd_bwd", part_fwd_bwd), ("batched", part_batched), ("modi", part_modi)):
+                result[name] = fn(dev, a, local_rank, peaks)
+                torch.cuda.empty_cache()
         if not a.no_cpu_baseline and world == 1:
             result["cpu_baseline"] = cpu_baseline(prob)
     return result
+
+
+# ----------------------------------------------------------------- the metric's other parts
+def _timed_clocked(fn, steps, warmup, index, flush=None):
+    """Mean ms of fn over `steps` calls, each bracketed by its own CUDA events
+    on the current stream (an L2 flush between calls, outside the events),
+    with nvidia-smi clocks sampled during the timed calls."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    with ClockSampler(index) as clk:
+        time.sleep(0.2)
+        for e0, e1 in ev:
+            if flush is not None:
+                flush.zero_()
+            e0.record()
+            fn()
+            e1.record()
+        torch.cuda.synchronize()
+    return statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev), clk.summary()
+
+
+def _roofline(units, t_fp32, t_sfu, t_mem, ms, kernel, sms, sm_max_mhz, hbm_gbs, peak_kind):
+    t_roof = max(t_fp32, t_sfu, t_mem)
+    term = "fp32" if t_roof == t_fp32 else "sfu" if t_roof == t_sfu else "hbm"
+    achieved = units / (ms / 1e3)
+    peak = units / t_roof
+    return {"bound": "alu", "term": term, "achieved": achieved / 1e9, "peak": peak / 1e9,
+            "unit": "Gnode·pt/s", "frac": achieved / peak, "traffic": None, "kernel": kernel,
+            "kernel_ms": ms,
+            "peak_basis": f"{sms} SMs x (FP32 128 / SFU 16 (ex2 32) lanes per clock) at "
+                          f"{sm_max_mhz:.0f} MHz, HBM {hbm_gbs} GB/s ({peak_kind})",
+            "t_fp32_ms": 1e3 * t_fp32, "t_sfu_ms": 1e3 * t_sfu, "t_hbm_ms": 1e3 * t_mem}
+
+
+def _targets_multi(api, prob, X, dev):
+    """y [D, O] = ground-truth trees (evaluated by the library) + noise."""
+    import torch
+    ys = []
+    for k in range(prob.gt.pop):
+        gt_t, gt_v, gt_s = api.population_to(prob.gt.take([k]), dev)
+        gy, _ = api.tgp_eval_forward(gt_t, gt_v, gt_s, X, 1, max_len=prob.gt.max_len)
+        ys.append(gy[0, 0])
+    return (torch.stack(ys, 1) + torch.from_numpy(prob.noise).to(dev)).contiguous()
+
+
+def part_fwd_bwd(dev, a, index, peaks):
+    """Differentiation workload: 10,000 trees <= 127 nodes (<= 16 constants),
+    200,000 points, F = 4 U(-3,3).  Forward + MSE, fused forward + adjoint
+    (gradients of sum(g * MSE) w.r.t. every constant and X), and one Adam step
+    on the constants through the autograd.Function."""
+    import torch
+    from paper_2501_17168_gb300 import api, autograd as ag, workloads as W
+    hbm_gbs, sm_max_mhz, peak_kind, sms = peaks
+    prob = W.diff(0)
+    t, v, s = api.population_to(prob.pop, dev)
+    X = torch.from_numpy(prob.X).to(dev)
+    y = _targets_multi(api, prob, X, dev)
+    P, D, L = prob.pop.pop, prob.D, prob.pop.max_len
+    g = torch.full((P, 1), 1.0 / P, dtype=torch.float64, device=dev)
+    gx = torch.zeros_like(X)
+    units = float(prob.pop.nodes()) * D
+    steps = max(a.steps, 3)
+    ms_f, clk_f = _timed_clocked(lambda: api.tgp_fitness_mse(t, v, s, X, y, 1, max_len=L), steps, 2,
+                                 index)
+    ms_fb, clk = _timed_clocked(lambda: api.tgp_eval_backward(t, v, s, X, y, g, 1, max_len=L, grad_X=gx),
+                                steps, 2, index)
+    api.tgp_check_device_error(dev)
+    # Adam on the constants gathered into [P, 16]
+    const = (t == W.CONST)
+    cnt = const.sum(1)
+    order = torch.argsort((~const).to(torch.int8), dim=1, stable=True)[:, :16]
+    mask = torch.arange(16, device=dev)[None, :] < cnt[:, None]
+    idx = torch.where(mask, order, torch.zeros_like(order))
+    consts = torch.gather(v, 1, idx).clone().requires_grad_(True)
+    opt = torch.optim.Adam([consts], lr=1e-2)
+
+    def adam_step():
+        val = v.scatter(1, idx, torch.where(mask, consts, torch.gather(v, 1, idx)))
+        mse = ag.fitness(val, X, t, s, y, 1, max_len=L)
+        loss = torch.nan_to_num(mse, nan=0.0, posinf=0.0).clamp(max=1e6).sum()
+        opt.zero_grad()
+        loss.backward()
+        consts.grad = torch.nan_to_num(consts.grad) * mask
+        opt.step()
+    ms_adam, _ = _timed_clocked(adam_step, min(steps, 20), 1, index)
+    t_fp32, t_sfu = _roofline_time_fwd_bwd(prob.pop, D, sms, sm_max_mhz * 1e6)
+    t_mem = (_bytes_once(prob.pop, D, prob.F) + 8.0 * D * prob.F + 12.0 * P * L) / (hbm_gbs * 1e9)
+    tf32_f, tsfu_f = _roofline_time(prob.pop, D, sms, sm_max_mhz * 1e6, hbm_gbs)
+    return {
+        "workload": f"diff: {P} trees len<=127 (<=16 constants) x {D} points, F={prob.F} U(-3,3); "
+                    "MSE gradient w.r.t. constants and X",
+        "node_points": units, "steps": steps,
+        "ms_forward_mse": ms_f, "ms_fwd_bwd": ms_fb, "ms_per_adam_step": ms_adam,
+        "fwd_bwd_over_forward": ms_fb / ms_f,
+        "node_points_per_s_fwd_bwd": units / (ms_fb / 1e3),
+        "forward_roofline_frac": 1e3 * max(tf32_f, tsfu_f) / ms_f,
+        "roofline": _roofline(units, t_fp32, t_sfu, t_mem, ms_fb, "adjoint (whole call)", sms,
+                              sm_max_mhz, hbm_gbs, peak_kind),
+        "clocks": clk, "clocks_forward": clk_f,
+    }
+
+
+def part_modi(dev, a, index, peaks):
+    """Multi-output workload: 20,000 Modi trees <= 255 nodes, 8 outputs,
+    1,000,000 points, F = 32 N(0,1).  Forward + per-output MSE on all points;
+    forward + adjoint on every 10th point (stated)."""
+    import torch
+    from paper_2501_17168_gb300 import api, workloads as W
+    hbm_gbs, sm_max_mhz, peak_kind, sms = peaks
+    prob = W.modi(0)
+    t, v, s = api.population_to(prob.pop, dev)
+    X = torch.from_numpy(prob.X).to(dev)
+    y = _targets_multi(api, prob, X, dev)
+    P, D, L, O = prob.pop.pop, prob.D, prob.pop.max_len, prob.gt.pop
+    units = float(prob.pop.nodes()) * D
+    steps = max(min(a.steps, 4), 2)
+    ms_f, clk = _timed_clocked(lambda: api.tgp_fitness_mse(t, v, s, X, y, O, max_len=L), steps, 1, index)
+    Xs, ys = X[::10].contiguous(), y[::10].contiguous()
+    g = torch.full((P, O), 1.0 / P, dtype=torch.float64, device=dev)
+    gx = torch.zeros_like(Xs)
+    ms_fb, clk_b = _timed_clocked(lambda: api.tgp_eval_backward(t, v, s, Xs, ys, g, O, max_len=L, grad_X=gx),
+                                  2, 1, index)
+    api.tgp_check_device_error(dev)
+    t_fp32, t_sfu = _roofline_time(prob.pop, D, sms, sm_max_mhz * 1e6, hbm_gbs, O)
+    t_mem = _bytes_once(prob.pop, D, prob.F, O) / (hbm_gbs * 1e9)
+    units_s = float(prob.pop.nodes()) * Xs.shape[0]
+    b_fp32, b_sfu = _roofline_time_fwd_bwd(prob.pop, Xs.shape[0], sms, sm_max_mhz * 1e6, O)
+    return {
+        "workload": f"modi: {P} Modi trees len<=255 x {D} points, F={prob.F} N(0,1), {O} outputs; "
+                    "forward + MSE (all points); forward + adjoint on every 10th point",
+        "node_points": units, "steps": steps,
+        "ms_forward_mse": ms_f, "node_points_per_s_forward": units / (ms_f / 1e3),
+        "roofline": _roofline(units, t_fp32, t_sfu, t_mem, ms_f, "eval_kernel<4,8,modi,mse> (whole call)",
+                              sms, sm_max_mhz, hbm_gbs, peak_kind),
+        "fwd_bwd_points": int(Xs.shape[0]), "ms_fwd_bwd_sample": ms_fb,
+        "ms_fwd_bwd_extrapolated_all_points": ms_fb * D / Xs.shape[0],
+        "fwd_bwd_roofline_frac": 1e3 * max(b_fp32, b_sfu) / ms_fb,
+        "node_points_per_s_fwd_bwd": units_s / (ms_fb / 1e3),
+        "clocks": clk, "clocks_fwd_bwd": clk_b,
+    }
+
+
+def part_batched(dev, a, index, peaks):
+    """Uneven batch: 8 independent SR problems (P 1k-20k, D 1k-1M log-uniform,
+    F 4-32, lengths U[7,511]) planned once with the autotuner's cache
+    (tgp_batch_plan) and run as one CUDA graph replay, against one
+    tgp_fitness_mse launch sequence per problem (library heuristic)."""
+    import tempfile
+    import torch
+    from paper_2501_17168_gb300 import api, autotune, workloads as W
+    hbm_gbs, sm_max_mhz, peak_kind, sms = peaks
+    probs = W.batched_uneven(0)
+    bps, units, t_fp32, t_sfu, t_mem = [], 0.0, 0.0, 0.0, 0.0
+    for pr in probs:
+        tt, vv, ss = api.population_to(pr.pop, dev)
+        Xp, yp = _gpu_targets(api, pr, dev)
+        bps.append(api.BatchProblem(tt, vv, ss, Xp, yp, 1, max_len=pr.pop.max_len))
+        units += pr.pop.nodes() * pr.D
+        f32, sfu = _roofline_time(pr.pop, pr.D, sms, sm_max_mhz * 1e6, hbm_gbs)
+        t_fp32 += f32
+        t_sfu += sfu
+        t_mem += _bytes_once(pr.pop, pr.D, pr.F) / (hbm_gbs * 1e9)
+    # autotune every problem into a cache file the C planner reads (points per
+    # lane fixed at 8 so that one launch variant serves all of them)
+    fd, cache = tempfile.mkstemp(prefix="tgp_tune_", suffix=".txt")
+    os.close(fd)
+    t0 = time.perf_counter()
+    for bp in bps:
+        tt, vv, ss, Xp, yp = bp.tensors
+        cands = [c for c in autotune.candidates(bp.pop.pop, bp.data.n_points, 1)
+                 if c and c.get("points_per_lane") == 8 and c.get("trees_per_block") >= 4]
+        autotune.tune(tt, vv, ss, Xp, yp, 1, max_len=bp.pop.max_len, reps=2, cands=cands, path=cache)
+    tune_s = time.perf_counter() - t0
+    plan = api.BatchPlan(bps, tune_cache=cache)
+    shapes = [plan.shape(i) for i in range(len(bps))]
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        plan.run()
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        plan.run()
+    steps = max(min(a.steps, 5), 2)
+    ms_graph, clk = _timed_clocked(graph.replay, steps, 1, index)
+    plan.check_device_error()
+
+    def per_problem():
+        for bp in bps:
+            tt, vv, ss, Xp, yp = bp.tensors
+            api.tgp_fitness_mse(tt, vv, ss, Xp, yp, 1, max_len=bp.pop.max_len, mse=bp.mse,
+                                tree_status=bp.status)
+    ms_each, clk_e = _timed_clocked(per_problem, steps, 1, index)
+    os.unlink(cache)
+    return {
+        "workload": "batched_uneven: 8 problems, " + ", ".join(
+            f"P={p.pop.pop} D={p.D} F={p.F}" for p in probs) + "; lengths U[7,511]; forward + MSE",
+        "node_points": units, "steps": steps,
+        "ms_graph_replay_autotuned_plan": ms_graph, "ms_one_launch_per_problem": ms_each,
+        "speedup_vs_one_launch_per_problem": ms_each / ms_graph,
+        "node_points_per_s": units / (ms_graph / 1e3),
+        "autotune_s": tune_s,
+        "shapes": [dict(sh, from_cache=fc) for sh, fc in shapes],
+        "roofline": _roofline(units, t_fp32, t_sfu, t_mem, ms_graph, "batched graph replay (whole)",
+                              sms, sm_max_mhz, hbm_gbs, peak_kind),
+        "clocks": clk, "clocks_per_problem": clk_e,
+    }
 
 
 def e2e(prob, dev, a, units):

@@ -104,8 +104,9 @@ typedef struct tgp_data {
   int64_t ldx;        /* row stride in elements, ldx >= n_features           */
 } tgp_data;
 
-/* Launch shape of the evaluation kernels.  Zero fields take the library's
- * heuristic; the autotuner fills them from measurements. */
+/* Launch shape of the evaluation kernels and call options.  Zero fields take
+ * the library's heuristic and defaults; the autotuner fills the shape fields
+ * from measurements. */
 typedef struct tgp_config {
   int32_t trees_per_block;  /* trees staged together in shared memory (1..64) */
   int32_t points_per_tile;  /* points of X staged per tile; a multiple of
@@ -115,7 +116,22 @@ typedef struct tgp_config {
   void* eval_begin_event;   /* optional cudaEvent_t recorded on the stream just
                                before the evaluation kernel(s), NULL = none  */
   void* eval_end_event;     /* optional cudaEvent_t recorded just after them  */
+  int32_t flags;            /* TGP_FLAG_* bits, 0 = none                     */
+  int32_t max_wait_polls;   /* limit of the bounded wait for the program
+                               copies: 0 = the library default (about 4 M
+                               polls, seconds); a negative value gives up at
+                               once, which drives the TGP_ERR_TIMEOUT path
+                               (tgp_check_device_error) without a fault      */
 } tgp_config;
+
+/* tgp_config.flags bits. */
+#define TGP_FLAG_SSE 1  /* MSE calls write the FP64 sum of squared residuals
+                           over this call's points instead of dividing it
+                           by n_points: the partial sums of a data set
+                           split by points across calls or ranks add up to
+                           D_total * MSE of the whole set (Sec. III-C
+                           fitness, sharded by points), and the caller
+                           divides once by D_total                        */
 
 /* Bytes of workspace the calls below need for these arguments (0 on invalid
  * arguments).  cfg may be NULL. */
@@ -154,8 +170,8 @@ typedef struct tgp_problem {
   int32_t n_outputs;
   double* mse;            /* [device] [pop, n_outputs] output                */
   int32_t* tree_status;   /* [device] [pop] output, or NULL                  */
-  tgp_config cfg;         /* launch shape (all zero = heuristic); the events
-                             are ignored                                     */
+  tgp_config cfg;         /* launch shape (all zero = heuristic) and flags;
+                             the events and max_wait_polls are ignored       */
 } tgp_problem;
 
 #define TGP_MAX_PROBLEMS 16
@@ -175,6 +191,59 @@ size_t tgp_batch_workspace_size(const tgp_problem* probs, int32_t n);
  * stream capture (the batched call of one generation is a CUDA graph). */
 tgp_status tgp_batch_fitness_mse(const tgp_problem* probs, int32_t n, void* ws, size_t ws_bytes,
                                  void* stream);
+
+/* Batch plan: the problems of tgp_batch_fitness_mse planned once on the host
+ * (launch shapes, workspace layout, launch grouping), then run any number of
+ * times.  tgp_batch_plan makes no CUDA call that touches the device's work
+ * (no allocation, no synchronization, no launch); it reads the device's SM
+ * count and shared-memory limit once per device.  The plan keeps a copy of
+ * the problem descriptors (the pointers in them, not the data): the buffers
+ * they name must stay valid, and their contents may change, between runs.
+ *   probs, n     as for tgp_batch_fitness_mse (1..TGP_MAX_PROBLEMS problems)
+ *   tune_cache   [host] path of the autotuner's cache file, or NULL.  For each
+ *                problem whose cfg shape fields are all zero, an entry for
+ *                this GPU and the problem's shape bucket (log2 of population,
+ *                points and max_len, features, outputs) supplies the launch
+ *                shape; otherwise the library's heuristic does.  A missing or
+ *                unreadable file is the same as NULL.  Format, one entry per
+ *                line ('#' starts a comment):
+ *                  <GPU name, spaces as '_'>|P<lg P>_D<lg D>_F<F>_O<O>_L<lg L>
+ *                  trees_per_block=<n> points_per_tile=<n> tiles_per_item=<n>
+ *                  points_per_lane=<n> [other name=value pairs are ignored]
+ *                (all on one line; lg x = log2(x) rounded to the nearest
+ *                integer).
+ *   plan         [host] out: the plan (host memory the library allocates with
+ *                malloc; release it with tgp_batch_free).
+ * Returns the same argument errors as tgp_batch_fitness_mse. */
+typedef struct tgp_batch_plan_s tgp_batch_plan_t;
+tgp_status tgp_batch_plan(const tgp_problem* probs, int32_t n, const char* tune_cache,
+                          tgp_batch_plan_t** plan);
+
+/* Host-only lookup in an autotuner cache file (the format of tgp_batch_plan):
+ * the launch shape stored for `key` (the whole first field of a line, e.g.
+ * "NVIDIA_GB300|P13_D17_F16_O1_L8"), the last line for the key winning.
+ * Makes no CUDA call.  Returns TGP_OK and fills the shape fields of *shape
+ * (the rest zero), or TGP_ERR_INVALID_ARG when the file, the key or a valid
+ * entry is missing. */
+tgp_status tgp_tune_cache_lookup(const char* tune_cache, const char* key, tgp_config* shape);
+
+/* Workspace bytes a run of the plan needs (0 for a NULL plan). */
+size_t tgp_batch_plan_workspace_size(const tgp_batch_plan_t* plan);
+
+/* Launch shape the plan chose for problem i (cfg events are NULL), so that a
+ * caller can see whether the cache or the heuristic supplied it.  Returns
+ * TGP_ERR_INVALID_ARG for a NULL plan or pointer or i out of range. */
+tgp_status tgp_batch_plan_shape(const tgp_batch_plan_t* plan, int32_t i, tgp_config* shape,
+                                int32_t* from_cache);
+
+/* Runs the plan: one stage launch, one persistent evaluation launch per
+ * occupancy group and one finalize launch on `stream`, exactly as
+ * tgp_batch_fitness_mse.  Legal in stream capture: a captured run is a CUDA
+ * graph that evaluates the batch every time it is replayed. */
+tgp_status tgp_batch_run(const tgp_batch_plan_t* plan, void* ws, size_t ws_bytes, void* stream);
+
+/* Releases a plan (NULL is ignored). */
+void tgp_batch_free(tgp_batch_plan_t* plan);
 
 /* Reverse-mode gradient of L = sum_{p,k} grad_mse[p,k] * MSE[p,k] (the
  * adjoint is not in the paper; it differentiates the Sec. III-C fitness).
@@ -337,6 +406,14 @@ tgp_status tgp_fitness_accuracy(const tgp_population* pop, const tgp_data* data,
 tgp_status tgp_fitness_mse_noalloc(const tgp_population* pop, const tgp_data* data,
                                    const float* y, int32_t n_outputs, double* mse,
                                    int32_t* tree_status, void* stream);
+
+/* tgp_check_device_error for the scratch array of tgp_fitness_mse_noalloc
+ * (whose callers never see a workspace pointer): reads and clears the error
+ * word the last no-allocation call left there, after synchronizing `stream`.
+ * Call it before the next no-allocation call, which clears the word.
+ * Returns TGP_OK, TGP_ERR_TIMEOUT (that call's results are not valid) or
+ * TGP_ERR_CUDA. */
+tgp_status tgp_check_device_error_noalloc(void* stream);
 
 /* Reads and clears the device error word left in ws by the last calls on
  * this workspace (a bounded wait that gave up).  Synchronizes `stream`.

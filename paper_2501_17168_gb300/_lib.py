@@ -37,7 +37,11 @@ class tgp_data(ctypes.Structure):
 class tgp_config(ctypes.Structure):
     _fields_ = [("trees_per_block", ctypes.c_int32), ("points_per_tile", ctypes.c_int32),
                 ("tiles_per_item", ctypes.c_int32), ("points_per_lane", ctypes.c_int32),
-                ("eval_begin_event", ctypes.c_void_p), ("eval_end_event", ctypes.c_void_p)]
+                ("eval_begin_event", ctypes.c_void_p), ("eval_end_event", ctypes.c_void_p),
+                ("flags", ctypes.c_int32), ("max_wait_polls", ctypes.c_int32)]
+
+
+FLAG_SSE = 1
 
 
 class tgp_problem(ctypes.Structure):
@@ -100,7 +104,17 @@ _SIGS = {
                                             ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                             ctypes.c_void_p]),
+    "tgp_batch_plan": (ctypes.c_int, [_P(tgp_problem), ctypes.c_int32, ctypes.c_char_p,
+                                      _P(ctypes.c_void_p)]),
+    "tgp_batch_plan_workspace_size": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "tgp_tune_cache_lookup": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_char_p, _P(tgp_config)]),
+    "tgp_batch_plan_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _P(tgp_config),
+                                            _P(ctypes.c_int32)]),
+    "tgp_batch_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                     ctypes.c_void_p]),
+    "tgp_batch_free": (None, [ctypes.c_void_p]),
     "tgp_check_device_error": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "tgp_check_device_error_noalloc": (ctypes.c_int, [ctypes.c_void_p]),
     "tgp_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "tgp_version": (ctypes.c_char_p, []),
 }

@@ -77,10 +77,12 @@ def make_config(cfg) -> tgp_config | None:
     for ev in (ev0, ev1):
         if ev is not None and not ev.cuda_event:
             ev.record()  # torch creates the CUDA event lazily on its first record
+    flags = int(cfg.get("flags", 0)) | (_lib.FLAG_SSE if cfg.get("sse") else 0)
     return tgp_config(int(cfg.get("trees_per_block", 0)), int(cfg.get("points_per_tile", 0)),
                       int(cfg.get("tiles_per_item", 0)), int(cfg.get("points_per_lane", 0)),
                       ev0.cuda_event if ev0 is not None else None,
-                      ev1.cuda_event if ev1 is not None else None)
+                      ev1.cuda_event if ev1 is not None else None,
+                      flags, int(cfg.get("max_wait_polls", 0)))
 
 
 def _cref(c):
@@ -258,6 +260,56 @@ def tgp_batch_fitness_mse(problems, ws=None):
     check(lib.tgp_batch_fitness_mse(arr, len(problems), ws.data_ptr(), ws.numel(), _stream_handle(dev)),
           "tgp_batch_fitness_mse")
     return [p.mse for p in problems]
+
+
+class BatchPlan:
+    """A batch planned once on the host (tgp_batch_plan) and run any number of
+    times (tgp_batch_run, legal in CUDA graph capture).  `tune_cache` is the
+    autotuner's cache file (None: the library's heuristic for every problem
+    without its own shape)."""
+
+    def __init__(self, problems, tune_cache=None):
+        lib = _lib.load()
+        self.problems = list(problems)   # keeps the tensors alive
+        arr = (_lib.tgp_problem * len(self.problems))(*[p.c_struct() for p in self.problems])
+        h = ctypes.c_void_p()
+        path = tune_cache.encode() if tune_cache else None
+        check(lib.tgp_batch_plan(arr, len(self.problems), path, ctypes.byref(h)), "tgp_batch_plan")
+        self._h = h
+        self.ws_bytes = int(lib.tgp_batch_plan_workspace_size(h))
+        self.device = self.problems[0].tensors[3].device
+        self.ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=self.device)
+
+    def shape(self, i: int):
+        """(launch shape dict, from_cache) the plan chose for problem i."""
+        c = tgp_config()
+        fc = ctypes.c_int32()
+        check(_lib.load().tgp_batch_plan_shape(self._h, i, ctypes.byref(c), ctypes.byref(fc)),
+              "tgp_batch_plan_shape")
+        return ({"trees_per_block": c.trees_per_block, "points_per_tile": c.points_per_tile,
+                 "tiles_per_item": c.tiles_per_item, "points_per_lane": c.points_per_lane},
+                bool(fc.value))
+
+    def run(self):
+        check(_lib.load().tgp_batch_run(self._h, self.ws.data_ptr(), self.ws.numel(),
+                                        _stream_handle(self.device)), "tgp_batch_run")
+        return [p.mse for p in self.problems]
+
+    def check_device_error(self):
+        check(_lib.load().tgp_check_device_error(self.ws.data_ptr(), self.ws.numel(),
+                                                 _stream_handle(self.device)),
+              "tgp_check_device_error")
+
+    def close(self):
+        if self._h:
+            _lib.load().tgp_batch_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------ genetic operators

@@ -2,8 +2,17 @@
 
 Measures candidate launch shapes (points per lane, trees per block, points
 per tile, tiles per item) of ``tgp_fitness_mse`` on the problem at hand with
-CUDA events, and caches the fastest per GPU and shape bucket in a JSON file
-(``$TGP_AUTOTUNE_CACHE``, default ``~/.cache/tgp_gb300/autotune.json``).
+CUDA events, and caches the fastest per GPU and shape bucket in a text file
+(``$TGP_AUTOTUNE_CACHE``, default ``~/.cache/tgp_gb300/autotune.txt``) that
+the C library reads itself: ``tgp_batch_plan(probs, n, cache_path, &plan)``
+takes the stored shape for every problem without its own, and
+``tgp_tune_cache_lookup`` reads one entry.  One entry per line:
+
+    <GPU name, spaces as '_'>|P<lg P>_D<lg D>_F<F>_O<O>_L<lg max_len> \
+        trees_per_block=<n> points_per_tile=<n> tiles_per_item=<n> points_per_lane=<n> ms=<t>
+
+(all on one line; lg x = log2(x) rounded to the nearest integer; '#' starts a
+comment; the last line of a key wins).
 
 The candidates span the two schedules of the paper's adaptive parallelism
 (Sec. III-C): many trees per block over small point tiles (population
@@ -12,34 +21,42 @@ over large point tiles (data parallelism, its mode for large D).
 """
 from __future__ import annotations
 
-import json
 import math
 import os
 import threading
 
-import torch
-
-from . import api
+SHAPE_FIELDS = ("trees_per_block", "points_per_tile", "tiles_per_item", "points_per_lane")
 
 _lock = threading.Lock()
 
 
 def cache_path() -> str:
     return os.environ.get("TGP_AUTOTUNE_CACHE",
-                          os.path.join(os.path.expanduser("~"), ".cache", "tgp_gb300", "autotune.json"))
+                          os.path.join(os.path.expanduser("~"), ".cache", "tgp_gb300", "autotune.txt"))
 
 
-def _bucket(P: int, D: int, F: int, O: int, max_len: int) -> str:
-    lg = lambda x: int(round(math.log2(max(int(x), 1))))
-    return f"P{lg(P)}_D{lg(D)}_F{F}_O{O}_L{lg(max_len)}"
+def lg(x: int) -> int:
+    """log2 rounded to the nearest integer (x < 1 counts as 1)."""
+    return int(round(math.log2(max(int(x), 1))))
 
 
-def _key(device, P, D, F, O, max_len) -> str:
-    name = torch.cuda.get_device_name(device).replace(" ", "_")
-    return f"{name}|{_bucket(P, D, F, O, max_len)}"
+def bucket(P: int, D: int, F: int, O: int, max_len: int) -> str:
+    return f"P{lg(P)}_D{lg(D)}_F{int(F)}_O{int(O)}_L{lg(max_len)}"
+
+
+def key(gpu_name: str, P, D, F, O, max_len) -> str:
+    return f"{gpu_name.replace(' ', '_')}|{bucket(P, D, F, O, max_len)}"
+
+
+def _device_key(device, P, D, F, O, max_len) -> str:
+    import torch
+    return key(torch.cuda.get_device_name(device), P, D, F, O, max_len)
 
 
 def candidates(P: int, D: int, O: int = 1):
+    """The heuristic ({}) plus points per lane x tile widths x tree blocks:
+    from one tree per block over wide tiles (the data-parallel schedule) to
+    32 trees per block over one-chunk tiles (the population-parallel one)."""
     out = [{}]  # the library's own shape heuristic
     for K in ((4,) if O > 1 else (8, 4)):
         ch = 32 * K
@@ -54,32 +71,70 @@ def candidates(P: int, D: int, O: int = 1):
     return out
 
 
-def _load():
-    p = cache_path()
-    if os.path.exists(p):
-        try:
-            return json.load(open(p))
-        except (OSError, ValueError):
-            return {}
-    return {}
+def format_entry(k: str, cfg: dict, ms: float | None = None) -> str:
+    fields = " ".join(f"{f}={int(cfg.get(f, 0))}" for f in SHAPE_FIELDS)
+    return f"{k} {fields}" + (f" ms={ms:.6g}" if ms is not None else "")
 
 
-def _store(db):
-    p = cache_path()
-    os.makedirs(os.path.dirname(p), exist_ok=True)
-    tmp = p + f".{os.getpid()}.tmp"
-    json.dump(db, open(tmp, "w"), indent=1, sort_keys=True)
-    os.replace(tmp, p)
+def parse(text: str) -> dict:
+    """{key: {shape fields..., 'ms': t}} of a cache file's text (last line wins)."""
+    db = {}
+    for line in text.splitlines():
+        tok = line.split()
+        if not tok or tok[0].startswith("#"):
+            continue
+        e = {}
+        for t in tok[1:]:
+            if "=" in t:
+                n, v = t.split("=", 1)
+                try:
+                    e[n] = float(v) if n == "ms" else int(v)
+                except ValueError:
+                    pass
+        db[tok[0]] = e
+    return db
 
 
-def lookup(device, P, D, F, O, max_len):
+def load(path: str | None = None) -> dict:
+    p = path or cache_path()
+    try:
+        with open(p) as f:
+            return parse(f.read())
+    except OSError:
+        return {}
+
+
+def store(entries: dict, path: str | None = None):
+    """Merges {key: (cfg, ms)} into the cache file (atomic replace)."""
+    p = path or cache_path()
     with _lock:
-        return _load().get(_key(device, P, D, F, O, max_len))
+        db = load(p)
+        for k, (cfg, ms) in entries.items():
+            db[k] = dict({f: int(cfg.get(f, 0)) for f in SHAPE_FIELDS}, ms=ms)
+        d = os.path.dirname(p)
+        if d:
+            os.makedirs(d, exist_ok=True)
+        tmp = p + f".{os.getpid()}.tmp"
+        with open(tmp, "w") as f:
+            f.write("# tgp launch-shape cache: <gpu>|<bucket> shape fields (read by tgp_batch_plan)\n")
+            for k in sorted(db):
+                e = db[k]
+                f.write(format_entry(k, e, e.get("ms")) + "\n")
+        os.replace(tmp, p)
 
 
-def tune(type_, val, size, X, y, n_outputs=1, max_len=None, reps=3, cands=None, store=True,
-         verbose=False):
-    """Times every candidate on this problem; returns (best config, table)."""
+def lookup(device, P, D, F, O, max_len, path: str | None = None):
+    e = load(path).get(_device_key(device, P, D, F, O, max_len))
+    return None if e is None else {f: e.get(f, 0) for f in SHAPE_FIELDS}
+
+
+def tune(type_, val, size, X, y, n_outputs=1, max_len=None, reps=3, cands=None, store_result=True,
+         path: str | None = None, verbose=False):
+    """Times every candidate on this problem; returns (best config, table).
+    The heuristic ({}) is stored as the shape it resolves to, so that the
+    cache entry always names a concrete shape."""
+    import torch
+    from . import api
     P, L = type_.shape
     D, F = X.shape
     max_len = max_len or L
@@ -101,10 +156,7 @@ def tune(type_, val, size, X, y, n_outputs=1, max_len=None, reps=3, cands=None, 
         if verbose:
             print(f"{best:9.3f} ms  {cfg}", flush=True)
     table.sort(key=lambda t: t[0])
-    best_cfg = table[0][1]
-    if store:
-        with _lock:
-            db = _load()
-            db[_key(X.device, P, D, F, n_outputs, max_len)] = dict(best_cfg, ms=table[0][0])
-            _store(db)
+    best_ms, best_cfg = table[0]
+    if store_result and any(best_cfg.get(f) for f in SHAPE_FIELDS):
+        store({_device_key(X.device, P, D, F, n_outputs, max_len): (best_cfg, best_ms)}, path)
     return best_cfg, table

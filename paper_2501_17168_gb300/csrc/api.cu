@@ -1,9 +1,12 @@
 // api.cu -- host side of the C ABI declared in include/tgp.h: argument
 // checks, launch-shape heuristic, workspace layout and kernel launches.  No
 // allocation, no synchronization; everything goes onto the caller's stream.
+#include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <new>
 
 #include "../../include/tgp.h"
 #include "tgp_internal.cuh"
@@ -32,6 +35,7 @@ struct DevInfo {
   bool init = false;
   int sms = 0;
   int smem_optin = 0;
+  char name[256] = {0};  // device name with spaces as '_' (autotune cache key)
 };
 std::mutex g_mu;
 DevInfo g_dev[kMaxDevices];
@@ -54,6 +58,11 @@ bool dev_info(DevInfo* out) {
     if (cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
         cudaSuccess)
       return false;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return false;
+    size_t i = 0;
+    for (; i + 1 < sizeof(d.name) && prop.name[i]; ++i) d.name[i] = prop.name[i] == ' ' ? '_' : prop.name[i];
+    d.name[i] = 0;
     d.init = true;
   }
   *out = d;
@@ -220,6 +229,7 @@ struct Planned {
   Shape sp, sm;     // plain / Modi kernel shapes, n_groups equalised
   WsLayout w;       // offsets relative to base
   size_t base;      // offset of this problem's workspace region
+  int flags = 0;    // TGP_FLAG_* of the problem
 };
 
 tgp_status plan(Planned& q, const tgp_config* cfg, bool mse, const DevInfo& dv, bool single) {
@@ -297,7 +307,7 @@ int carveout_step(size_t bytes) {
 }
 
 tgp_status launch_eval(Planned* qs, int n, char* ws, unsigned* counters, cudaStream_t st,
-                       const DevInfo& dv, bool mse) {
+                       const DevInfo& dv, bool mse, int max_polls = 0) {
   bool any_single = false;
   for (int i = 0; i < n; ++i) any_single |= qs[i].O == 1;
   const size_t limit = (size_t)dv.smem_optin;
@@ -374,6 +384,8 @@ tgp_status launch_eval(Planned* qs, int n, char* ws, unsigned* counters, cudaStr
       if (m == 0) continue;
       if (ngroup >= kMaxGroups) return TGP_ERR_UNSUPPORTED;
       b.counter = counters + CTRL_COUNTER_GROUP + 2 * ngroup++ + (modi ? 1 : 0);
+      b.err = counters + CTRL_ERROR;
+      b.max_polls = max_polls == 0 ? kDefaultWaitPolls : (max_polls < 0 ? 0 : max_polls);
       b.n = m;
       long long grid = (long long)dv.sms * per_sm;
       if (grid > total) grid = total;
@@ -401,6 +413,7 @@ tgp_status launch_final(Planned* qs, int n, char* ws, cudaStream_t st) {
     f.O = q.O;
     f.n_groups = q.sp.n_groups;
     f.D = q.data->n_points;
+    f.sse = (q.flags & TGP_FLAG_SSE) ? 1 : 0;
     total += q.pop->pop * q.O;
     b.end[m] = total;
     ++m;
@@ -426,8 +439,10 @@ tgp_status run(const tgp_population* pop, const tgp_data* data, const float* y, 
   if (!mse && pop->pop > 0 && data->n_points > 0 && !out) return TGP_ERR_INVALID_ARG;
   DevInfo dv;
   if (!dev_info(&dv)) return TGP_ERR_CUDA;
+  if (cfg && (cfg->flags & ~TGP_FLAG_SSE) != 0) return TGP_ERR_INVALID_ARG;
   Planned q{pop, data, y, O, out, mse_out, tree_status};
   q.base = 0;
+  q.flags = cfg ? cfg->flags : 0;
   tgp_status s = plan(q, cfg, mse, dv, true);
   if (s != TGP_OK) return s;
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < q.w.total) return TGP_ERR_WORKSPACE;
@@ -440,7 +455,8 @@ tgp_status run(const tgp_population* pop, const tgp_data* data, const float* y, 
   if (cfg && cfg->eval_begin_event &&
       cudaEventRecord(reinterpret_cast<cudaEvent_t>(cfg->eval_begin_event), st) != cudaSuccess)
     return TGP_ERR_CUDA;
-  s = launch_eval(&q, 1, wsb, reinterpret_cast<unsigned*>(wsb + q.w.ctrl), st, dv, mse);
+  s = launch_eval(&q, 1, wsb, reinterpret_cast<unsigned*>(wsb + q.w.ctrl), st, dv, mse,
+                  cfg ? cfg->max_wait_polls : 0);
   if (s != TGP_OK) return s;
   if (cfg && cfg->eval_end_event &&
       cudaEventRecord(reinterpret_cast<cudaEvent_t>(cfg->eval_end_event), st) != cudaSuccess)
@@ -452,19 +468,27 @@ tgp_status run(const tgp_population* pop, const tgp_data* data, const float* y, 
 // Several independent problems in one stage, one persistent evaluation and one
 // finalize launch.  Workspace: a 256-byte control block (the shared work
 // counters) followed by one region per problem.
-tgp_status plan_batch(const tgp_problem* probs, int n, const DevInfo& dv, Planned* qs, size_t* total) {
+bool shape_given(const tgp_config& c) {
+  return c.trees_per_block || c.points_per_tile || c.tiles_per_item || c.points_per_lane;
+}
+
+// tuned: NULL, or per problem a shape to use when the problem's own cfg gives
+// none (all shape fields zero = no tuned shape either).
+tgp_status plan_batch(const tgp_problem* probs, int n, const DevInfo& dv, Planned* qs, size_t* total,
+                      const tgp_config* tuned = nullptr) {
   if (n < 1 || n > TGP_MAX_PROBLEMS || !probs) return TGP_ERR_INVALID_ARG;
   size_t off = al256(CTRL_WORDS * 4);
   for (int i = 0; i < n; ++i) {
     const tgp_problem& p = probs[i];
     if (!problem_ok(&p.pop, &p.data, p.n_outputs)) return TGP_ERR_INVALID_ARG;
     if (p.data.n_points < 1 || (p.pop.pop > 0 && (!p.y || !p.mse))) return TGP_ERR_INVALID_ARG;
+    if ((p.cfg.flags & ~TGP_FLAG_SSE) != 0) return TGP_ERR_INVALID_ARG;
     Planned& q = qs[i];
     q = Planned{&p.pop, &p.data, p.y, p.n_outputs, nullptr, p.mse, p.tree_status};
-    const tgp_config* cfg = (p.cfg.trees_per_block || p.cfg.points_per_tile || p.cfg.tiles_per_item ||
-                             p.cfg.points_per_lane)
-                                ? &p.cfg
-                                : nullptr;
+    q.flags = p.cfg.flags;
+    const tgp_config* cfg = shape_given(p.cfg) ? &p.cfg
+                            : (tuned && shape_given(tuned[i])) ? &tuned[i]
+                                                                : nullptr;
     tgp_status s = plan(q, cfg, true, dv, false);
     if (s != TGP_OK) return s;
     q.base = off;
@@ -478,14 +502,12 @@ tgp_status plan_batch(const tgp_problem* probs, int n, const DevInfo& dv, Planne
   return TGP_OK;
 }
 
-tgp_status run_batch(const tgp_problem* probs, int n, void* ws, size_t ws_bytes, void* stream) {
-  DevInfo dv;
-  if (!dev_info(&dv)) return TGP_ERR_CUDA;
-  Planned qs[TGP_MAX_PROBLEMS];
-  size_t need = 0;
-  tgp_status s = plan_batch(probs, n, dv, qs, &need);
-  if (s != TGP_OK) return s;
+// Launches a planned batch (qs[0..n) with their workspace regions laid out
+// behind the shared control block).
+tgp_status launch_batch(Planned* qs, int n, size_t need, const DevInfo& dv, void* ws, size_t ws_bytes,
+                        void* stream) {
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < need) return TGP_ERR_WORKSPACE;
+  tgp_status s;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* wsb = reinterpret_cast<char*>(ws);
   if (cudaMemsetAsync(wsb, 0, CTRL_WORDS * 4, st) != cudaSuccess) return TGP_ERR_CUDA;
@@ -497,6 +519,68 @@ tgp_status run_batch(const tgp_problem* probs, int n, void* ws, size_t ws_bytes,
   s = launch_eval(qs, n, wsb, reinterpret_cast<unsigned*>(wsb), st, dv, true);
   if (s != TGP_OK) return s;
   return launch_final(qs, n, wsb, st);
+}
+
+tgp_status run_batch(const tgp_problem* probs, int n, void* ws, size_t ws_bytes, void* stream) {
+  DevInfo dv;
+  if (!dev_info(&dv)) return TGP_ERR_CUDA;
+  Planned qs[TGP_MAX_PROBLEMS];
+  size_t need = 0;
+  tgp_status s = plan_batch(probs, n, dv, qs, &need);
+  if (s != TGP_OK) return s;
+  return launch_batch(qs, n, need, dv, ws, ws_bytes, stream);
+}
+
+// ------------------------------------------------------------- autotune cache
+// Shape bucket of a problem, as the autotuner writes it:
+// <GPU name>|P<lg P>_D<lg D>_F<F>_O<O>_L<lg max_len>, lg = rounded log2.
+int lg_round(long long x) { return (int)std::lround(std::log2((double)(x < 1 ? 1 : x))); }
+
+void cache_key(const DevInfo& dv, const tgp_problem& p, char* out, size_t n) {
+  std::snprintf(out, n, "%s|P%d_D%d_F%d_O%d_L%d", dv.name, lg_round(p.pop.pop), lg_round(p.data.n_points),
+                (int)p.data.n_features, (int)p.n_outputs, lg_round(p.pop.max_len));
+}
+
+// Reads the entries of the cache file for the given keys (the last line of a
+// key wins).  Unknown names on a line are ignored; a malformed value leaves
+// the entry unused.
+void cache_read(const char* path, char (*keys)[320], int n, tgp_config* out, int* found) {
+  for (int i = 0; i < n; ++i) found[i] = 0;
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  char line[2048];
+  while (std::fgets(line, sizeof line, f)) {
+    char* save = nullptr;
+    char* tok = strtok_r(line, " \t\r\n", &save);
+    if (!tok || tok[0] == '#') continue;
+    int which = -1;
+    for (int i = 0; i < n; ++i)
+      if (std::strcmp(tok, keys[i]) == 0) which = i;
+    if (which < 0) continue;
+    tgp_config c{};
+    bool ok = true;
+    while ((tok = strtok_r(nullptr, " \t\r\n", &save)) != nullptr) {
+      char* eq = std::strchr(tok, '=');
+      if (!eq) continue;
+      *eq = 0;
+      char* end = nullptr;
+      const long v = std::strtol(eq + 1, &end, 10);
+      const bool num = end != eq + 1 && (*end == 0);
+      int32_t* dst = std::strcmp(tok, "trees_per_block") == 0   ? &c.trees_per_block
+                     : std::strcmp(tok, "points_per_tile") == 0 ? &c.points_per_tile
+                     : std::strcmp(tok, "tiles_per_item") == 0  ? &c.tiles_per_item
+                     : std::strcmp(tok, "points_per_lane") == 0 ? &c.points_per_lane
+                                                                : nullptr;
+      if (!dst) continue;
+      if (!num || v < 0 || v > 65536) ok = false;
+      else *dst = (int32_t)v;
+    }
+    // Every line for a key replaces the earlier one; a malformed line drops it.
+    found[which] = ok && shape_given(c) ? 1 : 0;
+    if (found[which]) out[which] = c;
+  }
+  std::fclose(f);
 }
 
 // Fused forward + reverse sweep: one CTA per point tile over all trees.
@@ -600,6 +684,19 @@ tgp_status run_backward(const tgp_population* pop, const tgp_data* data, const f
 }  // namespace
 }  // namespace tgp
 
+// A planned batch: copies of the problem descriptors, their launch shapes and
+// workspace layout, and the device they were planned for.
+struct tgp_batch_plan_s {
+  int n = 0;
+  int dev = -1;
+  size_t ws_bytes = 0;
+  tgp::DevInfo dv;
+  tgp_problem probs[TGP_MAX_PROBLEMS];
+  tgp::Planned qs[TGP_MAX_PROBLEMS];
+  tgp_config shape[TGP_MAX_PROBLEMS];
+  int from_cache[TGP_MAX_PROBLEMS];
+};
+
 using namespace tgp;
 
 extern "C" {
@@ -685,6 +782,92 @@ size_t tgp_batch_workspace_size(const tgp_problem* probs, int32_t n) {
 tgp_status tgp_batch_fitness_mse(const tgp_problem* probs, int32_t n, void* ws, size_t ws_bytes,
                                  void* stream) {
   return run_batch(probs, n, ws, ws_bytes, stream);
+}
+
+tgp_status tgp_batch_plan(const tgp_problem* probs, int32_t n, const char* tune_cache,
+                          tgp_batch_plan_t** plan) {
+  if (!plan) return TGP_ERR_INVALID_ARG;
+  *plan = nullptr;
+  if (!probs || n < 1 || n > TGP_MAX_PROBLEMS) return TGP_ERR_INVALID_ARG;
+  DevInfo dv;
+  if (!dev_info(&dv)) return TGP_ERR_CUDA;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TGP_ERR_CUDA;
+  tgp_batch_plan_s* pl = static_cast<tgp_batch_plan_s*>(std::calloc(1, sizeof(tgp_batch_plan_s)));
+  if (!pl) return TGP_ERR_INVALID_ARG;
+  new (pl) tgp_batch_plan_s();
+  pl->n = n;
+  pl->dev = dev;
+  pl->dv = dv;
+  for (int i = 0; i < n; ++i) pl->probs[i] = probs[i];
+  char keys[TGP_MAX_PROBLEMS][320];
+  tgp_config tuned[TGP_MAX_PROBLEMS] = {};
+  int found[TGP_MAX_PROBLEMS] = {};
+  for (int i = 0; i < n; ++i) {
+    cache_key(dv, pl->probs[i], keys[i], sizeof keys[i]);
+    pl->probs[i].cfg.eval_begin_event = pl->probs[i].cfg.eval_end_event = nullptr;
+  }
+  cache_read(tune_cache, keys, n, tuned, found);
+  tgp_status s = plan_batch(pl->probs, n, dv, pl->qs, &pl->ws_bytes, tuned);
+  if (s != TGP_OK) {
+    std::free(pl);
+    return s;
+  }
+  for (int i = 0; i < n; ++i) {
+    const bool own = shape_given(pl->probs[i].cfg);
+    pl->from_cache[i] = !own && found[i];
+    // the shape of the variant that serves the problem
+    const Shape& sh = pl->qs[i].O > 1 ? pl->qs[i].sm : pl->qs[i].sp;
+    tgp_config c{};
+    c.trees_per_block = sh.bt;
+    c.points_per_tile = sh.tp;
+    c.tiles_per_item = sh.g;
+    c.points_per_lane = sh.K;
+    c.flags = pl->probs[i].cfg.flags;
+    pl->shape[i] = c;
+  }
+  *plan = pl;
+  return TGP_OK;
+}
+
+size_t tgp_batch_plan_workspace_size(const tgp_batch_plan_t* plan) { return plan ? plan->ws_bytes : 0; }
+
+tgp_status tgp_tune_cache_lookup(const char* tune_cache, const char* key, tgp_config* shape) {
+  if (!tune_cache || !key || !shape || std::strlen(key) >= 320) return TGP_ERR_INVALID_ARG;
+  char keys[1][320];
+  std::strcpy(keys[0], key);
+  tgp_config c{};
+  int found = 0;
+  cache_read(tune_cache, keys, 1, &c, &found);
+  if (!found) return TGP_ERR_INVALID_ARG;
+  *shape = c;
+  return TGP_OK;
+}
+
+tgp_status tgp_batch_plan_shape(const tgp_batch_plan_t* plan, int32_t i, tgp_config* shape,
+                                int32_t* from_cache) {
+  if (!plan || !shape || i < 0 || i >= plan->n) return TGP_ERR_INVALID_ARG;
+  *shape = plan->shape[i];
+  if (from_cache) *from_cache = plan->from_cache[i];
+  return TGP_OK;
+}
+
+tgp_status tgp_batch_run(const tgp_batch_plan_t* plan, void* ws, size_t ws_bytes, void* stream) {
+  if (!plan) return TGP_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TGP_ERR_CUDA;
+  if (dev != plan->dev) return TGP_ERR_INVALID_ARG;
+  // the launches only read the plan; a run works on its own copy of the
+  // per-problem records so that concurrent runs of one plan do not interfere
+  Planned qs[TGP_MAX_PROBLEMS];
+  for (int i = 0; i < plan->n; ++i) qs[i] = plan->qs[i];
+  return launch_batch(qs, plan->n, plan->ws_bytes, plan->dv, ws, ws_bytes, stream);
+}
+
+void tgp_batch_free(tgp_batch_plan_t* plan) {
+  if (!plan) return;
+  plan->~tgp_batch_plan_s();
+  std::free(plan);
 }
 
 tgp_status tgp_check_device_error(void* ws, size_t ws_bytes, void* stream) {

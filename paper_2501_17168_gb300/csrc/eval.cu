@@ -64,12 +64,16 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
-// Bounded wait on an mbarrier phase: gives up after ~2^22 polls (each poll
-// itself suspends for a while), records the error and reports failure.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned* ctrl) {
-  for (int it = 0; it < (1 << 22); ++it)
+// Bounded wait on an mbarrier phase, run by ONE thread of the CTA: gives up
+// after max_polls polls (each poll itself suspends for a while; a negative
+// limit gives up at once), records the error and reports failure.  The
+// caller publishes the verdict through shared memory and a barrier so that
+// every thread of the CTA leaves (or goes on) together.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned* err,
+                                                  int max_polls) {
+  for (int it = 0; it < max_polls; ++it)
     if (mbar_try_wait(bar, parity)) return true;
-  atomicOr(&ctrl[CTRL_ERROR], (unsigned)ERR_MBAR_TIMEOUT);
+  atomicOr(err, (unsigned)ERR_MBAR_TIMEOUT);
   // give the copies still in flight a second bounded window to land before
   // the CTA (and its shared memory) goes away
   for (int it = 0; it < (1 << 20); ++it)
@@ -150,6 +154,7 @@ __global__ void __launch_bounds__(NW * 32, 3) eval_kernel(const __grid_constant_
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_all);
   long long* s_item = reinterpret_cast<long long*>(smem_all + 8);
   int* s_sub = reinterpret_cast<int*>(smem_all + 16);
+  int* s_ok = reinterpret_cast<int*>(smem_all + 20);
   unsigned char* smem = smem_all + 64;
   const long long total = b.end[b.n - 1];
 
@@ -246,9 +251,15 @@ __global__ void __launch_bounds__(NW * 32, 3) eval_kernel(const __grid_constant_
         order[rank] = t;
         lens[t] = Lt;
       }
-      if (!mbar_wait_bounded(mbar, phase, a.ctrl)) return;
-      phase ^= 1u;
+      // one thread waits for the copies; the verdict reaches every thread
+      // through shared memory, so the whole CTA returns (or goes on) together
+      if (tid == 0) *s_ok = mbar_wait_bounded(mbar, phase, b.err, b.max_polls) ? 1 : 0;
       __syncthreads();
+      if (*s_ok == 0) return;
+      // every thread observes the completed phase itself (succeeds at once),
+      // which orders its reads of the staged programs after the copies
+      (void)mbar_try_wait(mbar, phase);
+      phase ^= 1u;
 
       for (int gi = 0; gi < a.g; ++gi) {
         const long long tile = (long long)grp * a.g + gi;
@@ -373,7 +384,8 @@ __global__ void __launch_bounds__(NW * 32, 3) eval_kernel(const __grid_constant_
   }
 }
 
-// MSE[p,k] = (sum of the tile-group partials in order) / D; NaN for invalid trees.
+// MSE[p,k] = (sum of the tile-group partials in order) / D (the sum itself in
+// SSE mode); NaN for invalid trees.
 __global__ void finalize_kernel(const __grid_constant__ FinalBatch b) {
   const long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gi >= b.end[b.n - 1]) return;
@@ -384,7 +396,8 @@ __global__ void finalize_kernel(const __grid_constant__ FinalBatch b) {
   double s = 0.0;
   const double* src = a.partial + i * a.n_groups;
   for (int g = 0; g < a.n_groups; ++g) s += src[g];
-  a.mse[i] = a.status[p] != 0 ? __longlong_as_double(0x7ff8000000000000ll) : s / (double)a.D;
+  a.mse[i] = a.status[p] != 0 ? __longlong_as_double(0x7ff8000000000000ll)
+                               : (a.sse ? s : s / (double)a.D);
 }
 
 // ----------------------------------------------------------- host-side table

@@ -40,12 +40,21 @@ extern "C" tgp_status tgp_fitness_mse_noalloc(const tgp_population* pop, const t
                                               const float* y, int32_t n_outputs, double* mse,
                                               int32_t* tree_status, void* stream) {
   if (!pop || !data) return TGP_ERR_INVALID_ARG;
-  const size_t need = tgp_workspace_size(pop, data, n_outputs, nullptr);
-  if (need == 0) return TGP_ERR_INVALID_ARG;
-  if (need > (size_t)TGP_NOALLOC_WS_BYTES) return TGP_ERR_WORKSPACE;
+  // the device comes first, so that a CUDA failure is reported as such and
+  // not as the invalid-argument answer of the size query
   void* ws = nullptr;
   const tgp_status s = scratch_address(&ws);
   if (s != TGP_OK) return s;
+  const size_t need = tgp_workspace_size(pop, data, n_outputs, nullptr);
+  if (need == 0) return TGP_ERR_INVALID_ARG;
+  if (need > (size_t)TGP_NOALLOC_WS_BYTES) return TGP_ERR_WORKSPACE;
   return tgp_fitness_mse(pop, data, y, n_outputs, mse, tree_status, ws,
                          (size_t)TGP_NOALLOC_WS_BYTES, stream);
+}
+
+extern "C" tgp_status tgp_check_device_error_noalloc(void* stream) {
+  void* ws = nullptr;
+  const tgp_status s = scratch_address(&ws);
+  if (s != TGP_OK) return s;
+  return tgp_check_device_error(ws, (size_t)TGP_NOALLOC_WS_BYTES, stream);
 }

@@ -152,6 +152,7 @@ struct FinalArgs {
   long long pop;
   int O, n_groups;
   long long D;
+  int sse;            // 1: write the sum of squared residuals (no division by D)
 };
 
 struct AdjArgs {
@@ -201,7 +202,9 @@ struct StageBatch {
 
 struct EvalBatch {
   int n;
+  int max_polls;                     // bounded-wait limit (negative: give up at once)
   unsigned* counter;                 // work counter of this kernel variant
+  unsigned* err;                     // error word of the call (control block of ws)
   long long end[MAX_PROBLEMS];       // cumulative work items
   EvalArgs p[MAX_PROBLEMS];
 };
@@ -225,5 +228,8 @@ enum { CTRL_COUNTER = 0, CTRL_ANY_MODI = 1, CTRL_ERROR = 2, CTRL_COUNTER_MODI = 
        CTRL_COUNTER_GROUP = 8, CTRL_WORDS = 64 };
 // bits of the error word
 enum { ERR_MBAR_TIMEOUT = 1 };
+// polls of a bounded mbarrier wait before it gives up (each poll suspends the
+// thread for a while, so this is seconds)
+constexpr int kDefaultWaitPolls = 1 << 22;
 
 }  // namespace tgp

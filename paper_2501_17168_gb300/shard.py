@@ -8,8 +8,10 @@ beyond rounding:
     points and the per-tree sums of squared residuals are added across
     ranks (one all-reduce of pop * n_outputs doubles; `combine_point_shards`).
 The benchmark uses population replicas (weak scaling).  The point-sharded
-combination is what a rank-parallel caller of tgp_fitness_mse would run:
-    sse_r = mse_r * D_r;  SSE = all_reduce(sum, sse_r);  MSE = SSE / D.
+combination is what a rank-parallel caller runs: each rank calls
+tgp_fitness_mse_cfg with the TGP_FLAG_SSE flag, which returns the FP64 sum of
+squared residuals over its points (no division), then
+    SSE = all_reduce(sum, sse_r);  MSE = SSE / D_total.
 
 A generation (Algorithm 1) shards its fitness by population and replicates
 the rest: each rank evaluates its range of trees, one all-gather of P
@@ -33,16 +35,16 @@ def point_range(n_points: int, rank: int, world: int) -> tuple[int, int]:
     return population_range(n_points, rank, world)
 
 
-def combine_point_shards(mse_local, n_local: int, n_total: int, group=None):
-    """MSE over all points from each rank's MSE over its own points.
+def combine_point_shards(sse_local, n_total: int, group=None):
+    """MSE over all points from each rank's sum of squared residuals over its
+    own points (the TGP_FLAG_SSE output of tgp_fitness_mse_cfg; a rank with
+    no points passes zeros).
 
-    `mse_local` is a float64 tensor [pop, n_outputs] (NaN rows of invalid trees
+    `sse_local` is a float64 tensor [pop, n_outputs] (NaN rows of invalid trees
     stay NaN).  Uses one torch.distributed all_reduce (sum)."""
     import torch
     import torch.distributed as dist
-    sse = mse_local.to(torch.float64) * float(n_local)
-    if n_local == 0:
-        sse = torch.zeros_like(sse)
+    sse = sse_local.to(torch.float64).clone()
     dist.all_reduce(sse, op=dist.ReduceOp.SUM, group=group)
     return sse / float(n_total)
 

@@ -39,6 +39,35 @@ int main(void) {
   CHECK(tgp_tournament_select(NULL, 1, 10, NULL, 0, 20, 1, NULL, NULL) == TGP_OK);
   CHECK(tgp_tournament_select(NULL, 1, 10, NULL, 5, 20, 1, NULL, NULL) == TGP_ERR_INVALID_ARG);
   CHECK(tgp_accuracy_from_outputs(NULL, 0, 3, 10, NULL, NULL, NULL, NULL) == TGP_OK);
+
+  /* batch plan: argument checks and the host-only autotune cache lookup */
+  tgp_batch_plan_t* plan = NULL;
+  CHECK(tgp_batch_plan(NULL, 1, NULL, &plan) == TGP_ERR_INVALID_ARG && plan == NULL);
+  CHECK(tgp_batch_plan_workspace_size(NULL) == 0);
+  CHECK(tgp_batch_run(NULL, NULL, 0, NULL) == TGP_ERR_INVALID_ARG);
+  tgp_batch_free(NULL);
+  {
+    const char* path = "abi_smoke_tune.txt";
+    FILE* f = fopen(path, "w");
+    CHECK(f != NULL);
+    fprintf(f, "# comment\n");
+    fprintf(f, "GPU_X|P13_D17_F16_O1_L8 trees_per_block=8 points_per_tile=512 tiles_per_item=2 "
+               "points_per_lane=8 ms=1.5\n");
+    fprintf(f, "GPU_X|P13_D17_F16_O1_L8 trees_per_block=28 points_per_tile=1024 tiles_per_item=0 "
+               "points_per_lane=8\n");
+    fprintf(f, "GPU_X|P10_D10_F4_O1_L6 trees_per_block=x\n");
+    fclose(f);
+    tgp_config c;
+    memset(&c, 0, sizeof c);
+    CHECK(tgp_tune_cache_lookup(path, "GPU_X|P13_D17_F16_O1_L8", &c) == TGP_OK);
+    CHECK(c.trees_per_block == 28 && c.points_per_tile == 1024 && c.tiles_per_item == 0 &&
+          c.points_per_lane == 8 && c.flags == 0);
+    CHECK(tgp_tune_cache_lookup(path, "GPU_X|P10_D10_F4_O1_L6", &c) == TGP_ERR_INVALID_ARG);
+    CHECK(tgp_tune_cache_lookup(path, "GPU_Y|P13_D17_F16_O1_L8", &c) == TGP_ERR_INVALID_ARG);
+    CHECK(tgp_tune_cache_lookup("no_such_file.txt", "GPU_X|P13_D17_F16_O1_L8", &c) ==
+          TGP_ERR_INVALID_ARG);
+    remove(path);
+  }
   printf("ok\n");
   return 0;
 }

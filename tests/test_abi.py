@@ -113,6 +113,52 @@ def test_header_compiles_as_c_and_a_c_client_runs(lib, tmp_path):
            "-I", os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "c", "abi_smoke.c"),
            "-o", str(exe), "-L", build_dir, "-ltgp", f"-Wl,-rpath,{build_dir}"]
     subprocess.run(cmd, check=True, capture_output=True, text=True)
-    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120, cwd=str(tmp_path))
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == "ok"
+
+
+def test_autotune_cache_round_trip_through_the_c_reader(lib, tmp_path):
+    """The autotuner's cache file (written in Python) is what the C planner
+    reads: keys, candidates, store, lookup and the C parser agree."""
+    from paper_2501_17168_gb300 import autotune
+    assert autotune.lg(1) == 0 and autotune.lg(0) == 0 and autotune.lg(5000) == 12
+    assert autotune.lg(100_000) == 17 and autotune.lg(255) == 8 and autotune.lg(181) == 7
+    k = autotune.key("NVIDIA GB300", 5000, 100_000, 16, 1, 255)
+    assert k == "NVIDIA_GB300|P12_D17_F16_O1_L8"
+    # candidates: the heuristic first, both schedules (1 and 32 trees per
+    # block), tiles that are multiples of a warp's chunk and no wider than
+    # needed, one points-per-lane value for Modi populations
+    c = autotune.candidates(5000, 100_000, 1)
+    assert c[0] == {}
+    bts = {x["trees_per_block"] for x in c[1:]}
+    assert {1, 32} <= bts
+    for x in c[1:]:
+        assert x["points_per_tile"] % (32 * x["points_per_lane"]) == 0
+        assert x["points_per_tile"] <= 4096
+    small = autotune.candidates(3, 100, 1)
+    assert all(x["trees_per_block"] <= 3 for x in small[1:])
+    assert all(x["points_per_tile"] // 2 < 100 or x["points_per_tile"] == 32 * x["points_per_lane"]
+               for x in small[1:])
+    assert {x["points_per_lane"] for x in autotune.candidates(100, 1000, 8)[1:]} == {4}
+    path = str(tmp_path / "tune.txt")
+    autotune.store({k: ({"trees_per_block": 8, "points_per_tile": 512, "points_per_lane": 8}, 2.0)}, path)
+    autotune.store({k: ({"trees_per_block": 28, "points_per_tile": 1024, "tiles_per_item": 3,
+                         "points_per_lane": 8}, 1.0),
+                    "other|P1_D1_F1_O1_L1": ({"trees_per_block": 1, "points_per_tile": 128,
+                                               "points_per_lane": 4}, 5.0)}, path)
+    db = autotune.load(path)
+    assert db[k]["trees_per_block"] == 28 and db[k]["ms"] == 1.0
+    cfg = _lib.tgp_config()
+    assert lib.tgp_tune_cache_lookup(path.encode(), k.encode(), ctypes.byref(cfg)) == _lib.TGP_OK
+    assert (cfg.trees_per_block, cfg.points_per_tile, cfg.tiles_per_item, cfg.points_per_lane) == \
+        (28, 1024, 3, 8)
+    assert lib.tgp_tune_cache_lookup(path.encode(), b"other|P1_D1_F1_O1_L1", ctypes.byref(cfg)) == 0
+    assert cfg.points_per_lane == 4 and cfg.trees_per_block == 1
+    assert lib.tgp_tune_cache_lookup(path.encode(), b"missing", ctypes.byref(cfg)) == \
+        _lib.TGP_ERR_INVALID_ARG
+    # a malformed value drops the entry in both readers' view of validity
+    with open(path, "a") as f:
+        f.write(k + " trees_per_block=-3 points_per_tile=512\n")
+    assert lib.tgp_tune_cache_lookup(path.encode(), k.encode(), ctypes.byref(cfg)) == \
+        _lib.TGP_ERR_INVALID_ARG

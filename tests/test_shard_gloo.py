@@ -42,7 +42,9 @@ def _worker(rank, world, port, q):
     y = np.random.default_rng(0).standard_normal((prob.D, 1)).astype(np.float32)
     a, b = shard.point_range(prob.D, rank, world)
     m, _ = oracle.mse(prob.pop.type, prob.pop.val, prob.pop.size, prob.X[a:b], y[a:b], threads=1)
-    full = shard.combine_point_shards(torch.from_numpy(m), b - a, prob.D)
+    # each rank contributes its sum of squared residuals (what the library's
+    # TGP_FLAG_SSE mode returns); the oracle's mean times the local count is it
+    full = shard.combine_point_shards(torch.from_numpy(m * float(b - a)), prob.D)
     if rank == 0:
         ref, _ = oracle.mse(prob.pop.type, prob.pop.val, prob.pop.size, prob.X, y, threads=1)
         q.put(float(np.nanmax(np.abs(full.numpy() - ref) / np.maximum(np.abs(ref), 1e-300))))

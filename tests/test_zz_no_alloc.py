@@ -38,12 +38,13 @@ def _noalloc(lib, t, v, s, X, y, O, max_len):
     return rc, mse, st
 
 
-def _close(a, b):
+def _same(a, b):
+    """Bit-equal up to NaN payloads: both calls run the same kernels in the
+    same launch shape with fixed-order reductions, so any difference (a stale
+    value left in the shared scratch included) is a fault."""
     a, b = a.cpu().numpy(), b.cpu().numpy()
     both_nan = np.isnan(a) & np.isnan(b)
-    with np.errstate(invalid="ignore"):
-        ok = both_nan | (a == b) | (np.abs(a - b) <= 1e-4 * np.abs(b))
-    return bool(ok.all())
+    return bool((both_nan | (a.view(np.int64) == b.view(np.int64))).all())
 
 
 def test_noalloc_matches_workspace_call_twice(lib):
@@ -66,8 +67,11 @@ def test_noalloc_matches_workspace_call_twice(lib):
             rc, mse, st = _noalloc(lib, tt, vv, ss, Xd, yd, O, pop.max_len)
             torch.cuda.synchronize()
             assert rc == _lib.TGP_OK, lib.tgp_status_string(rc)
+            # the no-allocation call's own error word (no bounded wait gave up)
+            rc = lib.tgp_check_device_error_noalloc(torch.cuda.current_stream().cuda_stream)
+            assert rc == _lib.TGP_OK, lib.tgp_status_string(rc)
             assert torch.equal(st, st_ref)
-            assert _close(mse, ref), (call, O)
+            assert _same(mse, ref), (call, O)
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch(lib):
