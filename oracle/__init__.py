@@ -66,6 +66,9 @@ def _load():
             lib.orc_mse.restype = None
             lib.orc_grad.argtypes = [fp, fp, fp, L, L, I, fp, L, I, L, fp, L, I, dp, dp, dp, dp, ip, I]
             lib.orc_grad.restype = None
+            lib.orc_grad_bound.argtypes = [fp, fp, fp, L, L, I, fp, L, I, L, fp, L, I, dp, dp, dp, dp,
+                                           dp, dp, D, ip, I]
+            lib.orc_grad_bound.restype = None
             lib.orc_apply.argtypes = [I, D, D]
             lib.orc_apply.restype = D
             _lib = lib
@@ -140,8 +143,12 @@ def mse(type_, val, size, X, y, n_outputs=1, rel_tol=None, threads=None, max_len
     return (m, allow, st) if rel_tol is not None else (m, st)
 
 
-def grad(type_, val, size, X, y, g, n_outputs=1, threads=None, max_len=None):
-    """Reverse mode of sum(g * MSE): (mse [pop,O], grad_val [pop,ld], grad_X [D,F], status)."""
+def grad(type_, val, size, X, y, g, n_outputs=1, threads=None, max_len=None, with_err=False,
+         acc_terms=1024):
+    """Reverse mode of sum(g * MSE): (mse [pop,O], grad_val [pop,ld], grad_X [D,F], status);
+    with_err adds (egrad_val [pop,ld], egrad_X [D,F]): per element, a first-order
+    bound on how far an FP32 evaluation of the gradient may land (FP32 partial
+    sums of at most `acc_terms` contributions per constant before FP64)."""
     t, v, s = _pop(type_, val, size)
     X = _f32(X)
     y = _f32(y).reshape(X.shape[0], n_outputs)
@@ -152,12 +159,17 @@ def grad(type_, val, size, X, y, g, n_outputs=1, threads=None, max_len=None):
     gv = np.empty((pop, ld), np.float64)
     gx = np.empty((D, F), np.float64)
     st = np.zeros(pop, np.int32)
-    _load().orc_grad(_ptr(t, ctypes.c_float), _ptr(v, ctypes.c_float), _ptr(s, ctypes.c_float),
-                     pop, ld, ld if max_len is None else max_len, _ptr(X, ctypes.c_float), D, F, F,
-                     _ptr(y, ctypes.c_float), n_outputs, n_outputs, _ptr(g, ctypes.c_double),
-                     _ptr(m, ctypes.c_double), _ptr(gv, ctypes.c_double), _ptr(gx, ctypes.c_double),
-                     _ptr(st, ctypes.c_int), _threads(threads))
-    return m, gv, gx, st
+    egv = np.empty((pop, ld), np.float64) if with_err else None
+    egx = np.empty((D, F), np.float64) if with_err else None
+    _load().orc_grad_bound(_ptr(t, ctypes.c_float), _ptr(v, ctypes.c_float), _ptr(s, ctypes.c_float),
+                           pop, ld, ld if max_len is None else max_len, _ptr(X, ctypes.c_float), D, F, F,
+                           _ptr(y, ctypes.c_float), n_outputs, n_outputs, _ptr(g, ctypes.c_double),
+                           _ptr(m, ctypes.c_double), _ptr(gv, ctypes.c_double),
+                           _ptr(gx, ctypes.c_double),
+                           _ptr(egv, ctypes.c_double) if with_err else None,
+                           _ptr(egx, ctypes.c_double) if with_err else None,
+                           float(acc_terms), _ptr(st, ctypes.c_int), _threads(threads))
+    return (m, gv, gx, st, egv, egx) if with_err else (m, gv, gx, st)
 
 
 def apply(f: int, a: float, b: float = 0.0) -> float:

@@ -158,6 +158,7 @@ typedef struct {
   double* v;      /* value seen by the parent, per node          */
   double* fv;     /* function value (differs from v on Modi)     */
   int* c2;        /* index of the second child, per binary node  */
+  double* ev;     /* FP32 error bound of v, per node (or NULL)   */
 } ctx_t;
 
 static double apply(int f, double a, double b) {
@@ -183,11 +184,18 @@ static double apply(int f, double a, double b) {
  *   max           : exact
  *   sin, cos      : 2^-20.5 absolute + 1 u |v|  (approximation on the reduced
  *                   argument plus a two-part argument reduction)
- *   plog          : 2^-22 absolute + 2 u |v|    (log2 approximation times ln 2)
- *   cexp          : (6 + |a|) u |v|      (exp2 approximation, 2 ulp, and the
- *                   rounding of a*log2(e), which scales the result by |a| u)
- *   tan           : the sin/cos allowance divided by |cos a|, (1+|t|)^2 scaled
- * The FP32 implementation's own accuracy is checked against these numbers. */
+ *   plog          : 2^-22 absolute + 5 u |v|    (a base-2 logarithm accurate to
+ *                   2^-22 relative, 2^-22 absolute near 1, times ln 2 with a
+ *                   rounded product)
+ *   cexp          : (6 + 1.25 |a|) u |v| (exp2 approximation, 2 ulp, and the
+ *                   rounding of a*log2(e) with log2(e) itself rounded to
+ *                   float, which scales the result by up to 1.22 |a| u)
+ *   tan           : the sin/cos allowance divided by |cos a|, (1+|t|)^2
+ *                   scaled; infinite where the possible error of cos a
+ *                   reaches half of |cos a| (the first-order bound no longer
+ *                   holds: the quotient may take any size or sign)
+ * The FP32 implementation's own accuracy is checked against these numbers
+ * function by function over sweeps of exact arguments. */
 static double trig_abs(void) { return 6.9053396600248786e-07; /* 2^-20.5 */ }
 
 /* First-order FP32 error bound of f(a,b) given the operand bounds ea, eb.
@@ -226,13 +234,14 @@ static double err_of_raw(int f, double a, double ea, double b, double eb, double
       if (ea > 0 && fabs(fabs(a) - GUARD) <= ea) return INFINITY;
       if (!(fabs(a) > GUARD)) return 0.0;
       if (fabs(a) <= ea) return INFINITY;
-      return ea / (fabs(a) - ea) + ldexp(1.0, -22) + 2 * U32 * av;
+      return ea / (fabs(a) - ea) + ldexp(1.0, -22) + 5 * U32 * av;
     }
     case F_CEXP: {
       double am = fmin(a, EXP_CLAMP);
-      return av * expm1(ea) + av * (6 + fabs(am)) * U32;
+      return av * expm1(ea) + av * (6 + 1.25 * fabs(am)) * U32;
     }
     case F_TAN: {
+      if (2 * (fabs(sin(a)) * ea + 0.5 * ea * ea + trig_abs()) >= fabs(cos(a))) return INFINITY;
       double g = 1 + v * v, s = 1 + fabs(v);
       return g * ea + 2 * trig_abs() * s * s + U32 * av;
     }
@@ -251,10 +260,12 @@ static double eval_node(ctx_t* c, int i, int* next, double* err) {
     v = (double)c->x[(int)t->val[i]];
     *next = i + 1;
     if (c->v) { c->v[i] = v; c->fv[i] = v; }
+    if (c->ev) c->ev[i] = 0.0;
   } else if (base == T_CONST) {
     v = (double)t->val[i];
     *next = i + 1;
     if (c->v) { c->v[i] = v; c->fv[i] = v; }
+    if (c->ev) c->ev[i] = 0.0;
   } else {
     long iv = (long)t->val[i];
     int f = (int)(iv % 256);
@@ -289,6 +300,7 @@ static double eval_node(ctx_t* c, int i, int* next, double* err) {
       e = fe;
     }
     if (c->v) { c->v[i] = v; c->fv[i] = fv; }
+    if (c->ev) c->ev[i] = e;
   }
   *err = e;
   return v;
@@ -304,7 +316,7 @@ static int tree_has_modi(const tree_t* t) {
 static void eval_point(const tree_t* t, int has_modi, const float* x, int O,
                        double* out, double* eout, int want_err) {
   for (int k = 0; k < O; ++k) { out[k] = 0.0; if (eout) eout[k] = 0.0; }
-  ctx_t c = {t, x, out, eout, want_err, NULL, NULL, NULL};
+  ctx_t c = {t, x, out, eout, want_err, NULL, NULL, NULL, NULL};
   int nx;
   double e;
   double r = eval_node(&c, 0, &nx, &e);
@@ -336,6 +348,9 @@ typedef struct {
   const double* g;   /* grad: [pop][O] upstream gradient       */
   double* grad_val;  /* grad: [pop][ld]                        */
   double* grad_X;    /* grad: [D][F] (summed over threads)     */
+  double* egrad_val; /* grad: [pop][ld] FP32 error bound, or NULL */
+  double* egrad_X;   /* grad: [D][F] FP32 error bound, or NULL    */
+  double acc_terms;  /* grad bound: FP32 partial-sum length       */
   int* status;       /* [pop] validator status                 */
   int mode;          /* 0 eval, 1 mse, 2 grad                  */
   int nthreads;
@@ -344,7 +359,9 @@ typedef struct {
 typedef struct {
   job_t* j;
   int tid;
-  double* gx; /* private grad_X */
+  double* gx;  /* private grad_X                                   */
+  double* egx; /* private [D][F] error bound sums and [D][F] sums of
+                  |contribution| (bound mode only)                  */
 } worker_t;
 
 static void do_eval_tree(job_t* j, long p) {
@@ -460,7 +477,124 @@ static void backprop(ctx_t* c, int i, double adj, const double* seed,
   }
 }
 
-static void do_grad_tree(job_t* j, long p, double* gx_priv) {
+/* Local derivatives of f at (a, b) -- exactly those of backprop -- with
+ * first-order bounds of how far an FP32 evaluation of them may land, given
+ * the operand bounds ea, eb: the operands' errors carried through the second
+ * derivatives plus the allowance of the FP32 function that forms them.  A
+ * guard, clamp or max tie that the operand errors leave undecided makes
+ * both bounds infinite (the FP32 path may take the other branch). */
+static void dlocal(int f, double a, double ea, double b, double eb, double* da, double* eda,
+                   double* db, double* edb) {
+  *da = *db = *eda = *edb = 0.0;
+  int undecided = 0;
+  switch (f) {
+    case F_ADD: *da = 1; *db = 1; break;
+    case F_SUB: *da = 1; *db = -1; break;
+    case F_MUL: *da = b; *eda = eb; *db = a; *edb = ea; break;
+    case F_PDIV:
+      undecided = eb > 0 && fabs(fabs(b) - GUARD) <= eb;
+      if (fabs(b) > GUARD) {
+        double m = fabs(b) - eb;
+        *da = 1.0 / b;
+        *db = -a / (b * b);
+        if (!(m > 0)) { undecided = 1; break; }
+        *eda = eb / (fabs(b) * m) + 2 * U32 / fabs(b);
+        *edb = (ea + 2 * fabs(a) * eb / m) / (m * m) + 4 * U32 * fabs(a) / (b * b);
+      }
+      break;
+    case F_MAX:
+      if (a >= b || isnan(b)) *da = 1; else *db = 1;
+      /* an FP32 evaluation may route the adjoint to the other operand when
+       * the operands' errors leave the comparison undecided (exact operands
+       * compare exactly): each derivative may then be off by 1 (max itself
+       * is continuous, so its value's bound stays finite) */
+      if (!isnan(a) && !isnan(b) && ea + eb > 0 && fabs(a - b) <= ea + eb) *eda = *edb = 1.0;
+      break;
+    case F_SIN:
+      *da = cos(a);
+      *eda = fabs(sin(a)) * ea + 0.5 * ea * ea + trig_abs() + U32 * fabs(*da);
+      break;
+    case F_COS:
+      *da = -sin(a);
+      *eda = fabs(cos(a)) * ea + 0.5 * ea * ea + trig_abs() + U32 * fabs(*da);
+      break;
+    case F_PLOG:
+      undecided = ea > 0 && fabs(fabs(a) - GUARD) <= ea;
+      if (fabs(a) > GUARD) {
+        double m = fabs(a) - ea;
+        *da = 1.0 / a;
+        if (!(m > 0)) { undecided = 1; break; }
+        *eda = ea / (fabs(a) * m) + 2 * U32 / fabs(a);
+      }
+      break;
+    case F_CEXP:
+      undecided = ea > 0 && fabs(a - EXP_CLAMP) <= ea;
+      if (a <= EXP_CLAMP) {
+        *da = exp(a);
+        *eda = fabs(*da) * (expm1(ea) + (6 + 1.25 * fabs(a)) * U32);
+      }
+      break;
+    case F_TAN: {
+      double t = tan(a);
+      double et = err_of(F_TAN, a, ea, 0.0, 0.0, t);
+      *da = 1 + t * t;
+      *eda = 2 * fabs(t) * et + et * et + 2 * U32 * fabs(*da);
+      break;
+    }
+  }
+  if (undecided) *eda = *edb = INFINITY;
+}
+
+/* The reverse sweep of backprop carrying a first-order bound eadj on how far
+ * the FP32 adjoint of the value the parent sees at node i may be from adj.
+ * Per leaf it adds the adjoint, its bound and |adjoint| (for the allowance
+ * of the FP32 sums) into the constant and input-gradient accumulators. */
+static void backprop_err(ctx_t* c, int i, double adj, double eadj, const double* seed,
+                         const double* eseed, double* gval, double* egval, double* sgval,
+                         double* gx, double* egx, double* sgx) {
+  const tree_t* t = c->t;
+  int ty = (int)t->type[i];
+  int base = ty & ~T_MODI;
+  if (base == T_CONST) { gval[i] += adj; egval[i] += eadj; sgval[i] += fabs(adj); return; }
+  if (base == T_VAR) {
+    int f = (int)t->val[i];
+    gx[f] += adj; egx[f] += eadj; sgx[f] += fabs(adj);
+    return;
+  }
+  long iv = (long)t->val[i];
+  int f = (int)(iv % 256);
+  int o = (int)(iv / 256);
+  int ia = i + 1;
+  int ib = arity_of(f) == 2 ? c->c2[i] : -1;
+  double a = c->v[ia], ea = c->ev[ia];
+  double b = ib >= 0 ? c->v[ib] : 0.0, eb = ib >= 0 ? c->ev[ib] : 0.0;
+  double af = (ty & T_MODI) ? seed[o] : adj;
+  double eaf = (ty & T_MODI) ? eseed[o] : eadj;
+  double pass_a = 0.0, pass_b = 0.0, epass_a = 0.0, epass_b = 0.0;
+  if (ty & T_MODI) {
+    if (ib >= 0) { pass_b = adj; epass_b = eadj; } else { pass_a = adj; epass_a = eadj; }
+  }
+  double da, eda, db, edb;
+  dlocal(f, a, ea, b, eb, &da, &eda, &db, &edb);
+  /* one FP32 product (and one sum on a Modi node's pass-through) per child */
+  /* a zero local derivative contributes nothing (as in backprop), but its
+   * bound still counts: the FP32 path may see a non-zero one */
+  double ga = pass_a + (da != 0.0 ? af * da : 0.0);
+  double ega = epass_a + fabs(af) * eda + eaf * fabs(da) + eaf * eda + U32 * fabs(af * da) +
+               U32 * fabs(ga);
+  /* NaN (0 * inf) included; an adjoint that may leave the FP32 range too */
+  if (!(ega < INFINITY) || fabs(ga) + ega > FLT_MAX) ega = INFINITY;
+  backprop_err(c, ia, ga, ega, seed, eseed, gval, egval, sgval, gx, egx, sgx);
+  if (ib >= 0) {
+    double gb = pass_b + (db != 0.0 ? af * db : 0.0);
+    double egb = epass_b + fabs(af) * edb + eaf * fabs(db) + eaf * edb + U32 * fabs(af * db) +
+                 U32 * fabs(gb);
+    if (!(egb < INFINITY) || fabs(gb) + egb > FLT_MAX) egb = INFINITY;
+    backprop_err(c, ib, gb, egb, seed, eseed, gval, egval, sgval, gx, egx, sgx);
+  }
+}
+
+static void do_grad_tree(job_t* j, long p, double* gx_priv, double* egx_priv) {
   tree_t t = {j->type + p * j->ld, j->val + p * j->ld, j->size + p * j->ld, 0};
   int len;
   int st = orc_validate_one(t.type, t.val, t.size, j->max_len, j->F, j->O, &len);
@@ -470,33 +604,53 @@ static void do_grad_tree(job_t* j, long p, double* gx_priv) {
   for (long i = 0; i < j->ld; ++i) gval[i] = 0.0;
   if (st != ST_OK) {
     for (int k = 0; k < O; ++k) j->mse[p * O + k] = NAN;
+    if (j->egrad_val)
+      for (long i = 0; i < j->ld; ++i) j->egrad_val[p * j->ld + i] = INFINITY;
     return;
   }
   t.len = len;
   int hm = tree_has_modi(&t);
-  double* v = (double*)malloc(sizeof(double) * (size_t)len * 2);
+  const int we = j->egrad_val != NULL;
+  double* v = (double*)malloc(sizeof(double) * (size_t)len * 4);
   double* fv = v + len;
+  double* ev = v + 2 * (size_t)len;
+  double* sgval = v + 3 * (size_t)len;
   int* c2 = (int*)malloc(sizeof(int) * (size_t)len);
-  double* buf = (double*)calloc((size_t)O * 3, sizeof(double));
-  double *out = buf, *acc = buf + O, *seed = buf + 2 * O;
+  double* buf = (double*)calloc((size_t)O * 5, sizeof(double));
+  double *out = buf, *acc = buf + O, *seed = buf + 2 * O, *eout = buf + 3 * O, *eseed = buf + 4 * O;
+  double* egval = we ? j->egrad_val + p * j->ld : NULL;
+  if (we)
+    for (long i = 0; i < j->ld; ++i) egval[i] = 0.0;
+  for (int i = 0; i < len; ++i) sgval[i] = 0.0;
   int skip = 1;
   for (int k = 0; k < O; ++k) if (j->g[p * O + k] != 0.0) skip = 0;
   double inv_d = 1.0 / (double)j->D;
   for (long d = 0; d < j->D; ++d) {
-    for (int k = 0; k < O; ++k) out[k] = 0.0;
-    ctx_t c = {&t, j->X + d * j->ldx, out, NULL, 0, v, fv, c2};
+    for (int k = 0; k < O; ++k) { out[k] = 0.0; eout[k] = 0.0; }
+    ctx_t c = {&t, j->X + d * j->ldx, out, we ? eout : NULL, we, v, fv, c2, we ? ev : NULL};
     int nx;
     double e;
     double r0 = eval_node(&c, 0, &nx, &e);
-    if (!hm && O == 1) out[0] = r0;
+    if (!hm && O == 1) { out[0] = r0; eout[0] = e; }
     for (int k = 0; k < O; ++k) {
       double r = out[k] - (double)j->y[d * j->ldy + k];
       acc[k] += r * r;
       seed[k] = j->g[p * O + k] * 2.0 * r * inv_d;
+      /* the FP32 seed: (2g/D rounded) x (output - target, rounded) */
+      double s2 = fabs(j->g[p * O + k] * 2.0 * inv_d);
+      eseed[k] = s2 * (eout[k] + U32 * fabs(r)) + 2 * U32 * fabs(seed[k]);
+      if (!(eseed[k] < INFINITY)) eseed[k] = INFINITY;
     }
     if (skip) continue; /* zero upstream gradient: nothing to propagate */
     double* gxd = gx_priv + d * j->F;
-    if (!hm && O == 1) {
+    if (we) {
+      double* egxd = egx_priv + d * j->F;
+      double* sgxd = egx_priv + (size_t)j->D * j->F + d * j->F;
+      if (!hm && O == 1)
+        backprop_err(&c, 0, seed[0], eseed[0], seed, eseed, gval, egval, sgval, gxd, egxd, sgxd);
+      else
+        backprop_err(&c, 0, 0.0, 0.0, seed, eseed, gval, egval, sgval, gxd, egxd, sgxd);
+    } else if (!hm && O == 1) {
       backprop(&c, 0, seed[0], seed, gval, gxd);
     } else {
       /* the root's parent-visible value feeds no output */
@@ -504,6 +658,14 @@ static void do_grad_tree(job_t* j, long p, double* gx_priv) {
     }
   }
   for (int k = 0; k < O; ++k) j->mse[p * O + k] = acc[k] / (double)j->D;
+  /* an FP32 sum of at most acc_terms contributions before the widening to
+   * FP64 adds up to (acc_terms - 1) u times the sum of their magnitudes */
+  if (we)
+    for (int i = 0; i < len; ++i) {
+      egval[i] += (j->acc_terms > 1 ? j->acc_terms - 1 : 0) * U32 * sgval[i];
+      /* the gradient is delivered in FP32 */
+      if (!(egval[i] < INFINITY) || fabs(gval[i]) + egval[i] > FLT_MAX) egval[i] = INFINITY;
+    }
   free(v); free(c2); free(buf);
 }
 
@@ -513,7 +675,7 @@ static void* worker(void* arg) {
   for (long p = w->tid; p < j->pop; p += j->nthreads) {
     if (j->mode == 0) do_eval_tree(j, p);
     else if (j->mode == 1) do_mse_tree(j, p);
-    else do_grad_tree(j, p, w->gx);
+    else do_grad_tree(j, p, w->gx, w->egx);
   }
   return NULL;
 }
@@ -529,6 +691,8 @@ static void run_job(job_t* j) {
     ws[i].j = j;
     ws[i].tid = i;
     ws[i].gx = j->mode == 2 ? (double*)calloc(gxn > 0 ? gxn : 1, sizeof(double)) : NULL;
+    ws[i].egx = (j->mode == 2 && j->egrad_val) ? (double*)calloc(gxn > 0 ? 2 * gxn : 1, sizeof(double))
+                                                : NULL;
   }
   for (int i = 1; i < nt; ++i) pthread_create(&th[i], NULL, worker, &ws[i]);
   worker(&ws[0]);
@@ -538,8 +702,15 @@ static void run_job(job_t* j) {
       double s = 0.0;
       for (int i = 0; i < nt; ++i) s += ws[i].gx[q];
       j->grad_X[q] = s;
+      if (j->egrad_X) {
+        /* the FP32 sum over the trees adds (pop - 1) u |terms| */
+        double e = 0.0, m = 0.0;
+        for (int i = 0; i < nt; ++i) { e += ws[i].egx[q]; m += ws[i].egx[gxn + q]; }
+        e += (j->pop > 1 ? (double)(j->pop - 1) : 0.0) * U32 * m;
+        j->egrad_X[q] = (e < INFINITY && fabs(s) + e <= FLT_MAX) ? e : INFINITY;
+      }
     }
-    for (int i = 0; i < nt; ++i) free(ws[i].gx);
+    for (int i = 0; i < nt; ++i) { free(ws[i].gx); free(ws[i].egx); }
   }
   free(th);
   free(ws);
@@ -583,19 +754,42 @@ void orc_mse(const float* type, const float* val, const float* size, long pop, l
 }
 
 /* Reverse mode of L = sum_{p,k} g[p,k] * MSE[p,k]: grad_val[pop][ld] (nonzero
- * only at constant nodes) and grad_X[D][F]; also returns MSE[pop][O]. */
-void orc_grad(const float* type, const float* val, const float* size, long pop, long ld,
-              int max_len, const float* X, long D, int F, long ldx, const float* y, long ldy,
-              int O, const double* g, double* mse, double* grad_val, double* grad_X,
-              int* status, int nthreads) {
+ * only at constant nodes) and grad_X[D][F]; also returns MSE[pop][O].
+ * With egrad_val / egrad_X (both non-NULL) it also returns a first-order
+ * bound per element on how far an FP32 evaluation of the same gradient may
+ * land: the forward bounds of every node value and output, propagated
+ * through the seeds 2 g (o - y) / D and the local derivatives (dlocal), one
+ * FP32 rounding per product and sum, and FP32 partial sums of at most
+ * acc_terms contributions per constant (all trees' contributions per input
+ * element) before FP64.  Infinite where a guard, clamp or max tie is
+ * undecided or a value may leave the FP32 range. */
+void orc_grad_bound(const float* type, const float* val, const float* size, long pop, long ld,
+                    int max_len, const float* X, long D, int F, long ldx, const float* y, long ldy,
+                    int O, const double* g, double* mse, double* grad_val, double* grad_X,
+                    double* egrad_val, double* egrad_X, double acc_terms, int* status,
+                    int nthreads) {
   job_t j;
   memset(&j, 0, sizeof j);
   j.type = type; j.val = val; j.size = size; j.pop = pop; j.ld = ld; j.max_len = max_len;
   j.X = X; j.D = D; j.F = F; j.ldx = ldx; j.y = y; j.ldy = ldy; j.O = O;
   j.g = g; j.mse = mse; j.grad_val = grad_val; j.grad_X = grad_X; j.status = status;
+  j.egrad_val = egrad_X ? egrad_val : NULL;
+  j.egrad_X = egrad_val ? egrad_X : NULL;
+  j.acc_terms = acc_terms;
   j.mode = 2; j.nthreads = nthreads;
-  for (long q = 0; q < D * F; ++q) grad_X[q] = 0.0;
+  for (long q = 0; q < D * F; ++q) {
+    grad_X[q] = 0.0;
+    if (j.egrad_X) j.egrad_X[q] = 0.0;
+  }
   if (pop > 0) run_job(&j);
+}
+
+void orc_grad(const float* type, const float* val, const float* size, long pop, long ld,
+              int max_len, const float* X, long D, int F, long ldx, const float* y, long ldy,
+              int O, const double* g, double* mse, double* grad_val, double* grad_X,
+              int* status, int nthreads) {
+  orc_grad_bound(type, val, size, pop, ld, max_len, X, D, F, ldx, y, ldy, O, g, mse, grad_val,
+                 grad_X, NULL, NULL, 0.0, status, nthreads);
 }
 
 /* Single-function evaluation in FP64 (used to pin the function table). */

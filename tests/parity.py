@@ -74,3 +74,289 @@ def compare_mse(gpu, ref, allow):
         "skipped": int((~usable).sum()),
     }
     return res
+
+
+# ---------------------------------------------------------------- float32 floor
+# A plain float32 restatement of the tree semantics (numpy's float32 kernels:
+# correctly rounded +, -, *, /; sin, cos, log and exp within about one ulp),
+# evaluated on the same points.  Even such an evaluation misses the 1e-5 bar
+# on some points of deep random trees, so the GPU's strict fraction is held
+# against it: at least the restatement's fraction minus half a percentage
+# point, instead of a fixed floor.
+F32 = np.float32
+_GUARD32 = F32(1e-6)
+STRICT_MARGIN = 0.005
+
+
+def _apply32(f, a, b=None):
+    with np.errstate(all="ignore"):
+        if f == 0:
+            return a + b
+        if f == 1:
+            return a - b
+        if f == 2:
+            return a * b
+        if f == 3:
+            return np.where(np.abs(b) > _GUARD32, a / b, F32(1)).astype(F32)
+        if f == 4:
+            return np.fmax(a, b)
+        if f == 5:
+            return np.sin(a)
+        if f == 6:
+            return np.cos(a)
+        if f == 7:
+            return np.where(np.abs(a) > _GUARD32, np.log(np.abs(a)), F32(0)).astype(F32)
+        if f == 8:
+            return np.exp(np.minimum(a, F32(80)))
+        if f == 9:
+            return np.tan(a)
+    raise ValueError(f)
+
+
+def f32_eval(type_, val, size, X, n_outputs=1):
+    """Outputs [pop, n_outputs, D] of every valid tree in float32 (NaN rows for
+    trees whose length is not usable); stack evaluation from the end of the
+    prefix, the Modi rule of Sec. IV-C."""
+    X = np.asarray(X, F32)
+    type_, val, size = (np.atleast_2d(np.asarray(a, F32)) for a in (type_, val, size))
+    P, D = type_.shape[0], X.shape[0]
+    out = np.full((P, n_outputs, D), np.nan, F32)
+    for k in range(P):
+        L = size[k, 0]
+        if not np.isfinite(L) or L < 1 or L > type_.shape[1]:
+            continue
+        L = int(L)
+        acc = np.zeros((n_outputs, D), F32)
+        any_modi = False
+        stack = []
+        for i in range(L - 1, -1, -1):
+            t, v = int(type_[k, i]), val[k, i]
+            base, modi = t & ~16, bool(t & 16)
+            if base == 0:
+                stack.append(X[:, int(v)])
+                continue
+            if base == 1:
+                stack.append(np.full(D, v, F32))
+                continue
+            f, o = int(v) % 256, int(v) // 256
+            a = stack.pop()
+            b = stack.pop() if base == 3 else None
+            r = _apply32(f, a, b).astype(F32)
+            if modi:
+                any_modi = True
+                acc[o] = (acc[o] + r).astype(F32)
+                stack.append(b if b is not None else a)
+            else:
+                stack.append(r)
+        if n_outputs == 1 and not any_modi:
+            out[k, 0] = stack[-1]
+        else:
+            out[k] = acc
+    return out
+
+
+def strict_count(vals, ref, err):
+    """(usable, strict) points of `vals` under compare_points' masks."""
+    vals = np.asarray(vals, np.float64)
+    ref = np.asarray(ref, np.float64)
+    err = np.asarray(err, np.float64)
+    with np.errstate(all="ignore"):
+        usable = np.isfinite(err) & np.isfinite(ref)
+        strict = usable & (np.abs(vals - ref) <= TOL_POINT * np.maximum(np.abs(ref), 1.0))
+    return int(usable.sum()), int(strict.sum())
+
+
+def assert_strict_floor(gpu, ref, err, type_, val, size, X, n_outputs=1, tree_rows=None):
+    """The GPU's strict fraction is at least the float32 restatement's minus
+    STRICT_MARGIN on the same points; returns (gpu fraction, float32 fraction)."""
+    rows = slice(None) if tree_rows is None else tree_rows
+    v32 = f32_eval(np.asarray(type_)[rows], np.asarray(val)[rows], np.asarray(size)[rows], X, n_outputs)
+    n, s_gpu = strict_count(gpu, ref, err)
+    n2, s_32 = strict_count(v32, ref, err)
+    assert n == n2
+    f_gpu, f_32 = s_gpu / max(n, 1), s_32 / max(n, 1)
+    assert f_gpu >= f_32 - STRICT_MARGIN, (f"strict fraction {f_gpu:.4f} below the float32 "
+                                           f"restatement's {f_32:.4f} (n={n})")
+    return f_gpu, f_32
+
+
+def f32_mse(type_, val, size, X, y, n_outputs=1):
+    """MSE [pop, O] of the float32 restatement's outputs, summed in FP64."""
+    out = f32_eval(type_, val, size, X, n_outputs).astype(np.float64)
+    y = np.asarray(y, np.float64).reshape(X.shape[0], n_outputs)
+    with np.errstate(all="ignore"):
+        return np.mean((out - y.T[None]) ** 2, axis=2)
+
+
+def assert_mse_strict_floor(gpu_mse, ref, allow, type_, val, size, X, y, n_outputs=1):
+    """The GPU's count of MSEs within 1e-4 relative is at least the float32
+    restatement's minus max(1, STRICT_MARGIN * n)."""
+    m32 = f32_mse(type_, val, size, X, y, n_outputs)
+    r_gpu = compare_mse(gpu_mse, ref, allow)
+    r_32 = compare_mse(m32, ref, allow)
+    slack = max(1, int(STRICT_MARGIN * r_gpu["n"]))
+    assert r_gpu["strict"] >= r_32["strict"] - slack, (r_gpu["strict"], r_32["strict"], r_gpu["n"])
+    return r_gpu, r_32
+
+
+# ---------------------------------------------------------------- gradients
+TOL_GRAD = 1e-3
+
+
+def _children(type_row, val_row, L):
+    """First and second child of every node by an arity parse of the prefix."""
+    c1 = np.full(L, -1, np.int64)
+    c2 = np.full(L, -1, np.int64)
+    end = np.zeros(L, np.int64)
+    for i in range(L - 1, -1, -1):
+        base = int(type_row[i]) & ~16
+        if base <= 1:
+            end[i] = i + 1
+            continue
+        c1[i] = i + 1
+        if base == 3:
+            c2[i] = end[i + 1]
+            end[i] = end[c2[i]]
+        else:
+            end[i] = end[i + 1]
+    return c1, c2
+
+
+def f32_grad(type_, val, size, X, y, g, n_outputs=1):
+    """A plain float32 restatement of the reverse mode (numpy float32 kernels
+    per point; constant and input gradients summed over points and trees in
+    FP64): (grad_val [pop, ld], grad_X [D, F]) of sum(g * MSE)."""
+    X = np.asarray(X, F32)
+    type_, val, size = (np.atleast_2d(np.asarray(a, F32)) for a in (type_, val, size))
+    P, ld = type_.shape
+    D, Fn = X.shape
+    y = np.asarray(y, F32).reshape(D, n_outputs)
+    g = np.broadcast_to(np.asarray(g, np.float64), (P, n_outputs))
+    gval = np.zeros((P, ld))
+    gX = np.zeros((D, Fn))
+    with np.errstate(all="ignore"):
+        for k in range(P):
+            L = size[k, 0]
+            if not np.isfinite(L) or L < 1 or L > ld or not g[k].any():
+                continue
+            L = int(L)
+            tr, vr = type_[k], val[k]
+            c1, c2 = _children(tr, vr, L)
+            v = [None] * L
+            acc = np.zeros((n_outputs, D), F32)
+            any_modi = False
+            for i in range(L - 1, -1, -1):
+                base, modi = int(tr[i]) & ~16, bool(int(tr[i]) & 16)
+                if base == 0:
+                    v[i] = X[:, int(vr[i])]
+                    continue
+                if base == 1:
+                    v[i] = np.full(D, vr[i], F32)
+                    continue
+                f, o = int(vr[i]) % 256, int(vr[i]) // 256
+                a = v[c1[i]]
+                b = v[c2[i]] if c2[i] >= 0 else None
+                r = _apply32(f, a, b).astype(F32)
+                if modi:
+                    any_modi = True
+                    acc[o] = (acc[o] + r).astype(F32)
+                    v[i] = b if b is not None else a
+                else:
+                    v[i] = r
+            out = acc.copy()
+            if n_outputs == 1 and not any_modi:
+                out[0] = v[0]
+            seed = np.stack([F32(2.0 * g[k, q] / D) * (out[q] - y[:, q]).astype(F32)
+                             for q in range(n_outputs)]).astype(F32)
+            adj = [None] * L
+            adj[0] = seed[0] if (n_outputs == 1 and not any_modi) else np.zeros(D, F32)
+            for i in range(L):
+                base, modi = int(tr[i]) & ~16, bool(int(tr[i]) & 16)
+                if base == 1:
+                    gval[k, i] += float(np.sum(adj[i], dtype=np.float64))
+                    continue
+                if base == 0:
+                    gX[:, int(vr[i])] += adj[i]
+                    continue
+                f, o = int(vr[i]) % 256, int(vr[i]) // 256
+                a = v[c1[i]]
+                b = v[c2[i]] if c2[i] >= 0 else None
+                af = seed[o] if modi else adj[i]
+                one, zero = F32(1), F32(0)
+                da = db = None
+                if f == 0:
+                    da, db = np.ones(D, F32), np.ones(D, F32)
+                elif f == 1:
+                    da, db = np.ones(D, F32), -np.ones(D, F32)
+                elif f == 2:
+                    da, db = b, a
+                elif f == 3:
+                    big = np.abs(b) > _GUARD32
+                    rb = (one / b).astype(F32)
+                    da = np.where(big, rb, zero).astype(F32)
+                    db = np.where(big, -(a * rb) * rb, zero).astype(F32)
+                elif f == 4:
+                    left = (a >= b) | np.isnan(b)
+                    da, db = left.astype(F32), (~left).astype(F32)
+                elif f == 5:
+                    da = np.cos(a)
+                elif f == 6:
+                    da = -np.sin(a)
+                elif f == 7:
+                    da = np.where(np.abs(a) > _GUARD32, one / a, zero).astype(F32)
+                elif f == 8:
+                    da = np.where(a <= F32(80), np.exp(np.minimum(a, F32(80))), zero).astype(F32)
+                elif f == 9:
+                    t = np.tan(a)
+                    da = (one + t * t).astype(F32)
+                ga = np.where(da != 0, af * da, zero).astype(F32)
+                if modi and b is None:
+                    ga = (ga + adj[i]).astype(F32)
+                adj[c1[i]] = ga
+                if b is not None:
+                    gb = np.where(db != 0, af * db, zero).astype(F32)
+                    if modi:
+                        gb = (gb + adj[i]).astype(F32)
+                    adj[c2[i]] = gb
+    return gval, gX
+
+
+class GradStats:
+    def __init__(self):
+        self.n = self.strict = self.widened = self.skipped = 0
+
+    def __repr__(self):
+        return (f"elements={self.n} strict={self.strict} widened={self.widened} "
+                f"skipped={self.skipped}")
+
+
+def compare_grads(gpu, ref, bound, f32=None, stats=None):
+    """Per element: strict |gpu - ref| <= 1e-3 max(|ref|, 1), else within 2x
+    the oracle's first-order FP32 bound of the gradient (widened, counted);
+    elements whose bound is infinite are skipped and counted.  With a float32
+    restatement given, the GPU's strict count may fall short of the
+    restatement's by at most max(1, STRICT_MARGIN * n)."""
+    stats = stats or GradStats()
+    gpu, ref, bound = (np.asarray(a, np.float64) for a in (gpu, ref, bound))
+    with np.errstate(all="ignore"):
+        usable = np.isfinite(bound) & np.isfinite(ref)
+        tol = TOL_GRAD * np.maximum(np.abs(ref), 1.0)
+        d = np.abs(gpu - ref)
+        strict = usable & (d <= tol)
+        widened = usable & ~strict & (d <= 2 * bound)
+        bad = usable & ~strict & ~widened
+    if bad.any():
+        i = np.flatnonzero(bad.ravel())[:5]
+        raise AssertionError(f"{int(bad.sum())} gradient elements beyond the bar and 2x the bound: "
+                             f"gpu={gpu.ravel()[i]} ref={ref.ravel()[i]} bound={bound.ravel()[i]}")
+    stats.n += int(usable.sum())
+    stats.strict += int(strict.sum())
+    stats.widened += int(widened.sum())
+    stats.skipped += int((~usable).sum())
+    if f32 is not None:
+        f32 = np.asarray(f32, np.float64)
+        with np.errstate(all="ignore"):
+            s32 = int((usable & (np.abs(f32 - ref) <= tol)).sum())
+        n = int(usable.sum())
+        assert int(strict.sum()) >= s32 - max(1, int(STRICT_MARGIN * n)), (int(strict.sum()), s32, n)
+    return stats

@@ -27,8 +27,11 @@ def _built():
 
 def _bits_equal(a, b):
     a, b = a.cpu().numpy(), b.cpu().numpy()
+    if a.shape != b.shape or a.dtype != b.dtype:
+        return False
+    iv = np.int64 if a.dtype == np.float64 else np.int32
     both_nan = np.isnan(a) & np.isnan(b)
-    return bool((both_nan | (a.view(np.int64) == b.view(np.int64))).all())
+    return bool((both_nan | (a.view(iv) == b.view(iv))).all())
 
 
 def _problem(seed=3, P=150, D=5000, F=6):
@@ -94,7 +97,7 @@ def test_sse_mode_point_shards_add_up_to_the_mse(orc):
     assert (rel[fin & (fm < 1e30)] <= 1e-5).all(), np.nanmax(rel[fin & (fm < 1e30)])
     assert np.isnan(comb[~ok]).all()
     ref, allow, _ = orc.mse(p.type, p.val, p.size, X, y, rel_tol=1e-5)
-    r = compare_mse(comb, ref, allow)
+    r = compare_mse(comb[:, None], ref, allow)
     assert len(r["failed"]) == 0 and len(r["class_mismatch"]) == 0, r
 
 

@@ -2,12 +2,17 @@
 oracle's FP64 reverse mode and against central finite differences, plus the
 autograd.Function wrapper and a short Adam run on the constants.
 
-Gradients are sums over points of products of local partials; on trees
-whose forward evaluation is ill-conditioned at some point (the oracle's FP32
-bound exceeds the per-point tolerance) no FP32 evaluation can match FP64, so
-those trees get a zero upstream gradient (the library then skips them) and
-are counted.  The bar for the others: |gpu - ref| <= 1e-3 * max(|ref|, 1)
-elementwise.
+The oracle also bounds, per gradient element, how far an FP32 evaluation of
+the same gradient may land (its forward bounds carried through the seeds and
+local derivatives, one rounding per product and sum, FP32 partial sums before
+FP64).  Every element is checked: within the bar |gpu - ref| <= 1e-3 *
+max(|ref|, 1) (strict), or within 2x that bound where the bound says no FP32
+evaluation can meet the bar (widened, counted).  Only trees whose gradient
+bound is infinite somewhere (a guard, clamp or max tie the FP32 path may
+decide the other way, or an adjoint that may leave the FP32 range) get a
+zero upstream gradient and are counted; each test asserts the fraction of
+trees checked.  The GPU's strict count is held against a plain float32
+restatement of the reverse mode on the same elements.
 """
 import numpy as np
 import pytest
@@ -15,11 +20,13 @@ import pytest
 torch = pytest.importorskip("torch")
 
 from paper_2501_17168_gb300 import _lib, api, autograd as ag, workloads as W
+from parity import GradStats, compare_grads, f32_grad
 
 pytestmark = pytest.mark.gpu
 
 DEV = "cuda:0"
 TOL_GRAD = 1e-3
+ACC_TERMS = 512   # the adjoint kernel sums at most this many FP32 terms per constant before FP64
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -29,13 +36,15 @@ def _built():
     _lib.load()
 
 
-def well_conditioned(orc, p, X, O=1):
-    out, err, st = orc.evaluate(p.type, p.val, p.size, X, n_outputs=O, with_err=True,
-                                max_len=p.max_len)
-    with np.errstate(all="ignore"):
-        tol = 1e-5 * np.maximum(np.abs(out), 1.0)
-        good = np.isfinite(out) & (2 * err <= tol)
-    return (st == 0) & good.reshape(p.pop, -1).all(1)
+def gradient_checkable(orc, p, X, y, O=1):
+    """Trees whose oracle gradient bound is finite for every constant (one
+    oracle pass with g = 1 on every tree: constant bounds are per tree)."""
+    _, _, _, st, egv, _ = orc.grad(p.type, p.val, p.size, X, y, 1.0, n_outputs=O, max_len=p.max_len,
+                                   with_err=True, acc_terms=ACC_TERMS)
+    const = p.type == W.CONST
+    with np.errstate(invalid="ignore"):
+        fin = np.where(const, np.isfinite(egv), True).all(1)
+    return (st == 0) & fin
 
 
 def gpu_backward(p, X, y, g, O=1, want_mse=True):
@@ -49,28 +58,29 @@ def gpu_backward(p, X, y, g, O=1, want_mse=True):
     return cpu(mse), cpu(gv), cpu(gx), cpu(st)
 
 
-def check_grads(orc, p, X, y, O, rng, min_trees=20):
-    ok = well_conditioned(orc, p, X, O)
-    assert ok.sum() >= min_trees, ok.sum()
+def check_grads(orc, p, X, y, O, rng, min_frac=0.5):
+    ok = gradient_checkable(orc, p, X, y, O)
+    assert ok.mean() >= min_frac, (int(ok.sum()), p.pop)
     g = rng.uniform(0.5, 1.5, (p.pop, O)) * ok[:, None]
     mse, gv, gx, st = gpu_backward(p, X, y, g, O)
-    rm, rgv, rgx, rst = orc.grad(p.type, p.val, p.size, X, y, g, n_outputs=O, max_len=p.max_len)
+    rm, rgv, rgx, rst, egv, egx = orc.grad(p.type, p.val, p.size, X, y, g, n_outputs=O,
+                                           max_len=p.max_len, with_err=True, acc_terms=ACC_TERMS)
     np.testing.assert_array_equal(st, rst)
+    gv32, gx32 = f32_grad(p.type, p.val, p.size, X, y, g, O)
     # constant gradients of the included trees (zero elsewhere by contract)
     const = (p.type == W.CONST)
     sel = ok[:, None] & const
-    d = np.abs(gv[sel] - rgv[sel])
-    bad = d > TOL_GRAD * np.maximum(np.abs(rgv[sel]), 1.0)
-    assert not bad.any(), (int(bad.sum()), int(sel.sum()), float(d.max()))
+    sc = compare_grads(gv[sel], rgv[sel], egv[sel], f32=gv32[sel])
+    assert sc.skipped == 0, sc
     assert (gv[(st == 0)[:, None] & ~const] == 0).all()
     # input gradients (sum over the included trees)
-    dx = np.abs(gx - rgx)
-    badx = dx > TOL_GRAD * np.maximum(np.abs(rgx), 1.0)
-    assert not badx.any(), (int(badx.sum()), gx.size, float(dx.max()))
+    sx = compare_grads(gx, rgx, egx, f32=gx32)
+    assert sx.skipped <= 0.05 * gx.size, sx
     # fused MSE
     with np.errstate(all="ignore"):
         m_ok = ok[:, None] & np.isfinite(rm)
         assert (np.abs(mse[m_ok] - rm[m_ok]) <= 1e-4 * np.abs(rm[m_ok]) + 1e-12).all()
+    print(f"trees checked {int(ok.sum())}/{p.pop}; constants {sc}; inputs {sx}")
     return int(ok.sum()), int(sel.sum())
 
 
@@ -90,7 +100,7 @@ def test_backward_matches_oracle_tame(orc):
                             fset=(W.ADD, W.SUB, W.MUL, W.SIN, W.COS, W.MAX))
     X = rng.uniform(-1, 1, (600, 3)).astype(np.float32)
     y = rng.standard_normal((600, 1)).astype(np.float32)
-    n_ok, n_const = check_grads(orc, p, X, y, 1, rng, min_trees=150)
+    n_ok, n_const = check_grads(orc, p, X, y, 1, rng, min_frac=0.9)
     assert n_const > 500
 
 
@@ -100,7 +110,7 @@ def test_backward_modi(orc):
     p = prob.pop
     X = prob.X
     y = rng.standard_normal((700, 4)).astype(np.float32)
-    check_grads(orc, p, X, y, 4, rng, min_trees=10)
+    check_grads(orc, p, X, y, 4, rng)
 
 
 def test_backward_single_output_mixed_modi(orc):
@@ -110,7 +120,7 @@ def test_backward_single_output_mixed_modi(orc):
     P = W.stack([plain, modi])
     X = rng.uniform(-1, 1, (300, 2)).astype(np.float32)
     y = rng.standard_normal((300, 1)).astype(np.float32)
-    check_grads(orc, P, X, y, 1, rng, min_trees=40)
+    check_grads(orc, P, X, y, 1, rng, min_frac=0.7)
 
 
 def test_gpu_gradient_against_central_differences(orc):
@@ -248,4 +258,4 @@ def test_backward_sixteen_outputs(orc):
                             modi=True, modi_max=20, fset=(W.ADD, W.SUB, W.MUL, W.SIN, W.COS, W.MAX))
     X = rng.uniform(-1, 1, (400, 2)).astype(np.float32)
     y = rng.standard_normal((400, 16)).astype(np.float32)
-    check_grads(orc, p, X, y, 16, rng, min_trees=10)
+    check_grads(orc, p, X, y, 16, rng)

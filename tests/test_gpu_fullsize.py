@@ -14,12 +14,11 @@ import pytest
 torch = pytest.importorskip("torch")
 
 from paper_2501_17168_gb300 import _lib, api, workloads as W
-from parity import compare_mse
+from parity import assert_mse_strict_floor, assert_strict_floor, compare_mse, compare_points
 
 pytestmark = pytest.mark.gpu
 
 DEV = "cuda:0"
-TOL_GRAD = 1e-3
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -39,18 +38,25 @@ def _targets(orc, prob):
 
 
 def test_diff_full_size_adjoint_sampled(orc):
+    """Fused MSE, constant and X gradients at full size on 120 sampled trees.
+    Trees whose oracle gradient bound is finite for every constant get a
+    non-zero upstream gradient and are checked element by element (strict
+    1e-3 bar, or within 2x the bound, against a float32 restatement's strict
+    count); over 200,000 points close to half of the random trees meet a guard
+    or max tie that the FP32 path may decide the other way at some point, or
+    overflow, and are counted instead."""
+    from parity import compare_grads, f32_grad
     prob = W.diff()
     P, D = prob.pop.pop, prob.D
     y = _targets(orc, prob)
-    # over 200,000 points few deep random trees are well conditioned at every
-    # point, so sample widely and keep the well-conditioned ones
-    pick = np.arange(7, P, P // 240)
+    pick = np.arange(7, P, P // 120)
     sub = prob.pop.take(pick)
-    # trees whose forward is ill-conditioned at some point get no upstream gradient
-    out, err, st = orc.evaluate(sub.type, sub.val, sub.size, prob.X, with_err=True)
-    with np.errstate(all="ignore"):
-        good = (st == 0) & (np.isfinite(out) & (2 * err <= 1e-5 * np.maximum(np.abs(out), 1.0))).all(axis=(1, 2))
-    assert good.sum() >= 10, good.sum()
+    _, _, _, st0, egv0, _ = orc.grad(sub.type, sub.val, sub.size, prob.X, y, 1.0, max_len=sub.max_len,
+                                     with_err=True, acc_terms=512)
+    const = sub.type == W.CONST
+    with np.errstate(invalid="ignore"):
+        good = (st0 == 0) & np.where(const, np.isfinite(egv0), True).all(1)
+    assert good.mean() >= 0.4, (int(good.sum()), len(pick))
     rng = np.random.default_rng(5)
     g_sub = rng.uniform(0.5, 1.5, (len(pick), 1)) * good[:, None]
     g = np.zeros((P, 1))
@@ -61,35 +67,22 @@ def test_diff_full_size_adjoint_sampled(orc):
                                              torch.from_numpy(g).to(DEV), 1, max_len=prob.pop.max_len)
     api.tgp_check_device_error()
     mse, gv, gx, gst = (x.cpu().numpy() for x in (mse, gv, gx, gst))
-    rm, rgv, rgx, rst = orc.grad(sub.type, sub.val, sub.size, prob.X, y, g_sub, max_len=sub.max_len)
+    rm, rgv, rgx, rst, egv, egx = orc.grad(sub.type, sub.val, sub.size, prob.X, y, g_sub,
+                                           max_len=sub.max_len, with_err=True, acc_terms=512)
     np.testing.assert_array_equal(gst[pick], rst)
     # fused MSE of the sampled trees
     ref, allow, _ = orc.mse(sub.type, sub.val, sub.size, prob.X, y, rel_tol=1e-5)
     r = compare_mse(mse[pick], ref, allow)
     assert len(r["failed"]) == 0 and len(r["class_mismatch"]) == 0, r
-    # constant gradients of the sampled, included trees
-    const = sub.type == W.CONST
+    gv32, gx32 = f32_grad(sub.type, sub.val, sub.size, prob.X, y, g_sub)
+    # constant gradients of the included trees
     sel = good[:, None] & const
-    _check_grad(gv[pick][sel], rgv[sel])
-    assert sel.sum() >= 20
-    # X gradient: the sum over the sampled trees (every other tree has g = 0)
-    _check_grad(gx, rgx)
-
-
-def _check_grad(gpu, ref):
-    """Elementwise |gpu - ref| <= 1e-3 max(|ref|, 1); a derivative chain can
-    overflow although the forward values stay finite, so elements whose
-    reference is non-finite or above 1e30 must be so on the GPU too."""
-    gpu = np.asarray(gpu, np.float64)
-    ref = np.asarray(ref, np.float64)
-    with np.errstate(all="ignore"):
-        div_ref = ~np.isfinite(ref) | (np.abs(ref) > 1e30)
-        div_gpu = ~np.isfinite(gpu) | (np.abs(gpu) > 1e30)
-        assert (div_ref == div_gpu).all(), (int(div_ref.sum()), int(div_gpu.sum()))
-        d = np.abs(gpu - ref)[~div_ref]
-        bad = d > TOL_GRAD * np.maximum(np.abs(ref[~div_ref]), 1.0)
-    assert not bad.any(), (int(bad.sum()), float(d.max()))
-    assert div_ref.mean() < 0.01, float(div_ref.mean())
+    sc = compare_grads(gv[pick][sel], rgv[sel], egv[sel], f32=gv32[sel])
+    assert sc.skipped == 0 and sc.n >= 100, sc
+    # X gradient: the sum over the included sampled trees (every other tree has g = 0)
+    sx = compare_grads(gx, rgx, egx, f32=gx32)
+    assert sx.skipped <= 0.05 * gx.size, sx
+    print(f"trees checked {int(good.sum())}/{len(pick)}; constants {sc}; inputs {sx}")
 
 
 def test_modi_full_size_forward_sampled(orc):
@@ -102,12 +95,23 @@ def test_modi_full_size_forward_sampled(orc):
     api.tgp_check_device_error()
     m, st = m.cpu().numpy(), st.cpu().numpy()
     assert (st == 0).all()
-    pick = np.arange(3, P, P // 10)
+    # 200 sampled trees: MSE over all 1,000,000 points of the full launch
+    pick = np.arange(3, P, P // 200)
     sub = prob.pop.take(pick)
     ref, allow, ost = orc.mse(sub.type, sub.val, sub.size, prob.X, y, n_outputs=O, rel_tol=1e-5)
     r = compare_mse(m[pick].ravel(), ref.ravel(), allow.ravel())
     assert len(r["failed"]) == 0 and len(r["class_mismatch"]) == 0, r
     assert r["n"] >= len(pick) * O // 2, r
+    assert_mse_strict_floor(m[pick], ref, allow, sub.type, sub.val, sub.size, prob.X, y, O)
+    # per-point Modi outputs of the same trees on every 500th point
+    Xs = np.ascontiguousarray(prob.X[::500])
+    out, _ = api.tgp_eval_forward(t, v, s, torch.from_numpy(Xs).to(DEV), O, max_len=prob.pop.max_len)
+    out = out.cpu().numpy()[pick]
+    refp, err, _ = orc.evaluate(sub.type, sub.val, sub.size, Xs, n_outputs=O, with_err=True)
+    stats = compare_points(out, refp, err)
+    assert stats.failed == 0, (stats, stats.examples)
+    assert stats.n >= 0.9 * out.size, stats
+    assert_strict_floor(out, refp, err, sub.type, sub.val, sub.size, Xs, O)
 
 
 def test_batched_uneven_full_size_sampled(orc):
@@ -128,8 +132,10 @@ def test_batched_uneven_full_size_sampled(orc):
         # same kernels and shapes: one call per problem gives the same bits
         assert bool(((m1 == mb) | (torch.isnan(m1) & torch.isnan(mb))).all())
     for pr, y, mb in zip(probs, ys, batched):
-        pick = np.arange(1, pr.pop.pop, max(1, pr.pop.pop // 4))
+        pick = np.arange(1, pr.pop.pop, max(1, pr.pop.pop // 50))
         sub = pr.pop.take(pick)
         ref, allow, _ = orc.mse(sub.type, sub.val, sub.size, pr.X, y, rel_tol=1e-5)
         r = compare_mse(mb.cpu().numpy()[pick], ref, allow)
         assert len(r["failed"]) == 0 and len(r["class_mismatch"]) == 0, (pr.pop.pop, pr.D, r)
+        assert len(pick) >= 50
+        assert_mse_strict_floor(mb.cpu().numpy()[pick], ref, allow, sub.type, sub.val, sub.size, pr.X, y)

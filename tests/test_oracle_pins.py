@@ -578,3 +578,79 @@ def test_gpops_definition_reproduces_table():
     from paper_2501_17168_gb300.metrics import gpops
     g = GOLD["gpops"]
     assert gpops(g["G"], g["P"], g["S"], g["D"], g["T"]) == pytest.approx(g["gpops"], rel=5e-3)
+
+
+# ---------------------------------------------------------- gradient bound
+def test_gradient_bound_covers_float32_reverse_mode(orc):
+    """The oracle's per-element bound on the FP32 gradient covers a plain
+    float32 restatement of the reverse mode (numpy float32 per point, FP64
+    sums, so no FP32 partial sums: acc_terms = 1) on random single-output
+    and Modi populations."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from parity import f32_grad
+    rng = np.random.default_rng(3)
+    cases = []
+    p = W.random_population(31, 300, 63, (1, 63), max_depth=8, n_features=3, max_consts=16)
+    cases.append((p, rng.standard_normal((200, 3)).astype(np.float32),
+                  rng.standard_normal((200, 1)).astype(np.float32), 1))
+    q = W.random_population(32, 200, 31, (1, 31), max_depth=6, n_features=2,
+                            fset=(W.ADD, W.SUB, W.MUL, W.SIN, W.COS, W.MAX))
+    cases.append((q, rng.uniform(-1, 1, (150, 2)).astype(np.float32),
+                  rng.standard_normal((150, 1)).astype(np.float32), 1))
+    m = W.modi(pop=100, D=150, n_outputs=3)
+    cases.append((m.pop, m.X, rng.standard_normal((150, 3)).astype(np.float32), 3))
+    n_c = n_x = 0
+    for p, X, y, O in cases:
+        rm, rgv, rgx, rst, egv, egx = orc.grad(p.type, p.val, p.size, X, y, 1.0, n_outputs=O,
+                                               with_err=True, acc_terms=1)
+        gv32, gx32 = f32_grad(p.type, p.val, p.size, X, y, 1.0, O)
+        const = p.type == W.CONST
+        with np.errstate(all="ignore"):
+            okc = const & np.isfinite(egv)
+            okx = np.isfinite(egx)
+            assert not (np.abs(gv32 - rgv) > egv)[okc].any()
+            assert not (np.abs(gx32 - rgx) > egx)[okx].any()
+        n_c += int(okc.sum())
+        n_x += int(okx.sum())
+    assert n_c > 2000 and n_x > 1000
+
+
+def test_gradient_bound_is_tight_on_well_conditioned_trees(orc):
+    """For c * x0 and sin(c * x0 + x1) over well-scaled data the bound is a
+    small multiple of u times the sum of the magnitudes of the contributions
+    (not vacuous), and it grows with the FP32 partial-sum length; the max
+    rule's undecided ties count as a unit derivative error, guards left
+    undecided by their operand's error make the bound infinite."""
+    u = 2.0 ** -24
+    rng = np.random.default_rng(4)
+    X = rng.uniform(0.5, 2, (400, 2)).astype(np.float32)
+    y = np.zeros((400, 1), np.float32)
+    for toks in (["mul", ("c", 0.75), ("x", 0)],
+                 ["sin", "add", "mul", ("c", 0.75), ("x", 0), ("x", 1)]):
+        p = _enc(toks)
+        _, gv, gx, st, egv, egx = orc.grad(p.type, p.val, p.size, X, y, 1.0, with_err=True, acc_terms=1)
+        c = int(np.flatnonzero(p.type[0] == W.CONST)[0])
+        out, _ = orc.evaluate(p.type, p.val, p.size, X)
+        # per point |adjoint of c| = |2 o / D * do/dc| <= 2 |o| |x0| / D here
+        mag = np.sum(2 * np.abs(out[0, 0]) * X[:, 0].astype(np.float64) / 400)
+        assert 0 < egv[0, c] <= 64 * u * mag, (egv[0, c], mag)
+        _, _, _, _, egv2, _ = orc.grad(p.type, p.val, p.size, X, y, 1.0, with_err=True, acc_terms=400)
+        assert egv2[0, c] >= egv[0, c] + 300 * u * abs(gv[0, c])
+    # max(x0, x0 + c) at c = 0 and c tiny: an exact tie is decided, a tie the
+    # rounding of x0 + c may break is a unit derivative error
+    # (the adjoint reaches x0 through the max, so the input gradient shows it)
+    p = _enc(["mul", ("c", 1.0), "max", ("x", 0), "add", ("x", 0), ("c", 1e-9)])
+    _, gv, gx, _, egv, egx = orc.grad(p.type, p.val, p.size, X, y, 1.0, with_err=True, acc_terms=1)
+    assert np.isfinite(egx[:, 0]).all() and (egx[:, 0] > 0.1 * np.abs(gx[:, 0])).all()
+    assert egv[0, 1] <= 64 * u * np.sum(np.abs(gx[:, 0] * X[:, 0]))
+    p = _enc(["mul", ("c", 1.0), "max", ("x", 0), ("x", 0)])
+    _, gv, gx, _, egv, egx = orc.grad(p.type, p.val, p.size, X, y, 1.0, with_err=True, acc_terms=1)
+    assert (egx[:, 0] <= 64 * u * np.abs(gx[:, 0])).all()
+    # a protected division whose divisor lies within its error of the guard
+    p = _enc(["pdiv", ("c", 1.0), "sub", "mul", ("x", 0), ("x", 1), ("x", 2)])
+    Xg = np.array([[3.0, 1.0 / 3.0, 1.0 - 1e-6]], np.float32)
+    out, err, _ = orc.evaluate(p.type, p.val, p.size, Xg, with_err=True)
+    _, _, _, _, egv, _ = orc.grad(p.type, p.val, p.size, Xg, np.zeros((1, 1), np.float32), 1.0,
+                                  with_err=True)
+    assert not np.isfinite(err[0, 0, 0]) and np.isinf(egv[0, 1])
