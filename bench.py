@@ -73,7 +73,7 @@ def _args():
     ap.add_argument("--suite", action="store_true",
                     help="also time the other workloads (one JSON line each, after the main line)")
     ap.add_argument("--case", default=None,
-                    choices=["adjoint", "modi", "batched", "genetic", "sweep"],
+                    choices=["adjoint", "modi", "batched", "genetic", "sweep", "e1"],
                     help="time only one case for profiling: the fused forward + adjoint on the "
                          "differentiation workload or the Modi forward (--pop/--points), the "
                          "8-problem uneven batch (one batched call, then one call per problem), "
@@ -950,6 +950,59 @@ def sweep_lines(dev, steps):
     return out
 
 
+E1_POPULATION_PARALLEL = {"points_per_lane": 8, "trees_per_block": 32, "points_per_tile": 256}
+E1_DATA_PARALLEL = {"points_per_lane": 8, "trees_per_block": 1, "points_per_tile": 4096}
+
+
+def e1_lines(dev, steps):
+    """Threshold study of Sec. V-B on GB300: the Pagie polynomial, populations
+    100 / 1,000 / 5,000 / 10,000, data sets of 64 .. 262,144 points.  Per
+    (P, D): the fitness call in the library's population-parallel shape (32
+    trees per block over one 256-point chunk: the analogue of the paper's
+    hybrid schedule), its data-parallel shape (one tree per block over
+    4,096-point tiles: the analogue of the paper's one-tree-per-launch
+    schedule), the library's heuristic and the autotuner's pick, each timed
+    with CUDA events; then, per population, the crossover: the smallest D at
+    which the data-parallel shape is at least as fast."""
+    import torch
+    from paper_2501_17168_gb300 import api, autotune, workloads as W
+    big = W.e1_population(0, max(W.E1_POPS))
+    lens = big.lengths()
+    t, v, s = api.population_to(big, dev)
+    out, cross = [], {}
+    for D in W.E1_POINTS:
+        Xn, yn = W.e1_data(0, D)
+        X, y = torch.from_numpy(Xn).to(dev), torch.from_numpy(yn).to(dev)
+        for P in W.E1_POPS:
+            tt, vv, ss = t[:P], v[:P], s[:P]
+            units = float(lens[:P].sum()) * D
+            reps = steps if P * D <= 2 ** 27 else 2
+            ms = {}
+            for name, cfg in (("population_parallel", E1_POPULATION_PARALLEL),
+                              ("data_parallel", E1_DATA_PARALLEL), ("heuristic", None)):
+                ms[name] = _timed_events(
+                    lambda cfg=cfg: api.tgp_fitness_mse(tt, vv, ss, X, y, 1, max_len=256, config=cfg),
+                    reps, 1)
+            cands = [c for c in autotune.candidates(P, D, 1) if c.get("points_per_lane", 8) == 8]
+            best, table = autotune.tune(tt, vv, ss, X, y, 1, max_len=256, reps=1, cands=cands,
+                                        store_result=False)
+            ms["autotuned"] = _timed_events(
+                lambda: api.tgp_fitness_mse(tt, vv, ss, X, y, 1, max_len=256, config=best or None),
+                reps, 1)
+            api.tgp_check_device_error(dev)
+            line = {"case": "e1", "pop": P, "n_points": D, "node_points": units,
+                    "ms": ms, "autotuned_shape": best,
+                    "node_points_per_s": {k: units / (m / 1e3) for k, m in ms.items()}}
+            out.append(line)
+            if P not in cross and ms["data_parallel"] <= ms["population_parallel"]:
+                cross[P] = D
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    out.append({"case": "e1_crossover", "smallest_D_data_parallel_not_slower": cross,
+                "sm_count": sms, "sm_count_x_128": sms * 128,
+                "paper_threshold_rtx3090": 10_496})
+    return out
+
+
 def run_case(a):
     """One small case for the kernel profiles: the fused forward + adjoint of
     the differentiation workload (constants and inputs), or the Modi forward
@@ -958,6 +1011,10 @@ def run_case(a):
     from paper_2501_17168_gb300 import api, build, workloads as W
     build.build_all()
     dev = torch.device("cuda", 0)
+    if a.case == "e1":
+        for line in e1_lines(dev, a.steps):
+            print(json.dumps(line), flush=True)
+        return 0
     if a.case == "sweep":
         for line in sweep_lines(dev, a.steps):
             print(json.dumps(line), flush=True)

@@ -616,7 +616,7 @@ def main():
         "__device__ __forceinline__ unsigned interp_fwd(unsigned pg, unsigned xc, unsigned xstr,",
         "                                               unsigned mo, unsigned sb, float (&acc)[K]);",
     ]
-    for K, modi in ((8, False), (4, False), (4, True)):  # the kernels instantiated in eval.cu
+    for K, modi in ((8, False), (4, False), (8, True), (4, True)):  # the kernels instantiated in eval.cu
         parts.append(render(K, modi))
     parts.append("}  // namespace tgp")
     open(OUT, "w").write("\n".join(parts) + "\n")

@@ -299,6 +299,32 @@ def sweep_data(seed: int, name: str) -> tuple[np.ndarray, np.ndarray]:
             r.standard_normal((D, 1), dtype=np.float32))
 
 
+# ------------------------------------------------- threshold study inputs
+#: population sizes and data-set sizes of the threshold study (Sec. V-B: the
+#: Pagie polynomial at populations 100, 1,000, 5,000 and 10,000 over a sweep
+#: of data-set sizes across the hybrid / data-parallel switch)
+E1_POPS = (100, 1000, 5000, 10_000)
+E1_POINTS = (64, 256, 1024, 4096, 10_496, 16_384, 65_536, 262_144)
+
+
+def e1_population(seed: int = 0, pop: int = 10_000) -> Population:
+    """Random SR trees for the threshold study: the paper's function set,
+    lengths U[1, 255] in rows of 256, two features (x, y)."""
+    return random_population(_seed64(seed, 12), pop, 256, (1, 255), max_depth=12,
+                             fset=PAPER_FSET, n_features=2)
+
+
+def e1_data(seed: int, D: int) -> tuple[np.ndarray, np.ndarray]:
+    """Pagie polynomial data (Sec. V-B): (x, y) ~ U(-5, 5) and the target
+    f = 1/(1 + x^-4) + 1/(1 + y^-4) = x^4/(1 + x^4) + y^4/(1 + y^4), formed
+    in FP64 and rounded (a data-generating function, not a tree)."""
+    r = _rng(seed, 12, D)
+    X = r.uniform(-5, 5, (D, 2)).astype(np.float32)
+    x4 = X.astype(np.float64) ** 4
+    y = (x4[:, 0] / (1 + x4[:, 0]) + x4[:, 1] / (1 + x4[:, 1])).astype(np.float32)[:, None]
+    return X, y
+
+
 # ------------------------------------------------- genetic-operator inputs
 def random_words(seed: int, shape, *key: int) -> np.ndarray:
     """Uniform 32-bit words (the random numbers the operators consume)."""

@@ -26,7 +26,7 @@ pytestmark = pytest.mark.gpu
 
 DEV = "cuda:0"
 TOL_GRAD = 1e-3
-ACC_TERMS = 512   # the adjoint kernel sums at most this many FP32 terms per constant before FP64
+from parity import ACC_TERMS  # FP32 terms per constant before FP64 in the adjoint kernel
 
 
 @pytest.fixture(scope="module", autouse=True)
