@@ -99,7 +99,7 @@ bool shape_for_k(int K, long long P, long long D, int F, int O, int max_len, con
   Shape s{};
   s.nw = kNW;
   s.K = K;
-  if (s.K != 4 && s.K != 8) return false;
+  if (s.K != 4 && s.K != 8 && !(s.K == 16 && !modi)) return false;
   const int CH = 32 * s.K;
   const int pcap = pcap_of(max_len);
   s.bt = (cfg && cfg->trees_per_block) ? cfg->trees_per_block : 32;
@@ -155,21 +155,19 @@ bool shape_for_k(int K, long long P, long long D, int F, int O, int max_len, con
   return true;
 }
 
-// Launch shape: 8 points per lane unless the caller says otherwise or the
-// shared memory of a wide feature set (or, for Modi populations, of the
-// per-warp output accumulators) does not fit, then 4.  A single problem of
-// at most 128 points also takes 4: a warp's 256 slots at 8 per lane would
-// leave most lanes idle (60 points: 14% faster with 4 per lane, measured).
-// A batch keeps 8 for single-output problems and 4 for Modi problems so that
-// the problems of one launch share one kernel variant.
+// Launch shape: 8 points per lane for single-output populations unless the
+// caller says otherwise or the X tile of a wide feature set does not fit,
+// then 4; Modi populations always 4 (their accumulators live in shared
+// memory, and the Modi interpreter at 8 points per lane no longer fits the
+// instruction cache: 2.6x slower, measured).  A single problem of at most
+// 128 points also takes 4: a warp's 256 slots at 8 per lane would leave most
+// lanes idle (60 points: 14% faster with 4 per lane, measured).  A batch
+// keeps 8 so that its problems share one kernel variant.
 bool choose_shape(long long P, long long D, int F, int O, int max_len, const tgp_config* cfg,
                   bool modi, bool mse, const DevInfo& dv, Shape* sh, bool single) {
+  if (modi) return shape_for_k(4, P, D, F, O, max_len, cfg, modi, mse, dv, sh);
   if (cfg && cfg->points_per_lane)
     return shape_for_k(cfg->points_per_lane, P, D, F, O, max_len, cfg, modi, mse, dv, sh);
-  if (modi) {
-    if (single && D > 32 * 4 && shape_for_k(8, P, D, F, O, max_len, cfg, modi, mse, dv, sh)) return true;
-    return shape_for_k(4, P, D, F, O, max_len, cfg, modi, mse, dv, sh);
-  }
   if (single && D <= 32 * 4 && shape_for_k(4, P, D, F, O, max_len, cfg, modi, mse, dv, sh))
     return true;
   return shape_for_k(8, P, D, F, O, max_len, cfg, modi, mse, dv, sh) ||

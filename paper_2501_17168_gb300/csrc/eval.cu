@@ -82,26 +82,25 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 // ----------------------------------------------------------- lane points
-// A lane owns K points of a chunk of 32*K: for K = 8 the points
-// 4*lane + {0..3} and 128 + 4*lane + {0..3}; for K = 4 the points
-// 4*lane + {0..3}.  Both halves are one 16-byte shared-memory load.
+// A lane owns K points of a chunk of 32*K: the points 128*h + 4*lane +
+// {0..3} for h < K/4, each group of four one 16-byte shared-memory load.
 template <int K>
 __device__ __forceinline__ void ld_pts(float (&v)[K], const float* p) {
-  float4 u = *reinterpret_cast<const float4*>(p);
-  v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w;
-  if constexpr (K == 8) {
-    float4 w = *reinterpret_cast<const float4*>(p + 128);
-    v[4] = w.x; v[5] = w.y; v[6] = w.z; v[7] = w.w;
+#pragma unroll
+  for (int h = 0; h < K / 4; ++h) {
+    const float4 u = *reinterpret_cast<const float4*>(p + 128 * h);
+    v[4 * h] = u.x; v[4 * h + 1] = u.y; v[4 * h + 2] = u.z; v[4 * h + 3] = u.w;
   }
 }
 template <int K>
 __device__ __forceinline__ void st_pts(float* p, const float (&v)[K]) {
-  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-  if constexpr (K == 8) *reinterpret_cast<float4*>(p + 128) = make_float4(v[4], v[5], v[6], v[7]);
+#pragma unroll
+  for (int h = 0; h < K / 4; ++h)
+    *reinterpret_cast<float4*>(p + 128 * h) = make_float4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
 }
 template <int K>
 __device__ __forceinline__ int pt_index(int lane, int j) {
-  return (j < 4) ? 4 * lane + j : 128 + 4 * lane + (j - 4);
+  return 128 * (j >> 2) + 4 * lane + (j & 3);
 }
 
 // ----------------------------------------------------------- smem layout
@@ -146,7 +145,7 @@ __host__ __device__ inline EvalSmem eval_smem_layout(int K, int nw, bool modi, b
 
 // ----------------------------------------------------------- kernel
 template <int K, int NW, bool MODI, bool OUT>
-__global__ void __launch_bounds__(NW * 32, 3) eval_kernel(const __grid_constant__ EvalBatch b) {
+__global__ void __launch_bounds__(NW * 32, K >= 16 ? 2 : 3) eval_kernel(const __grid_constant__ EvalBatch b) {
   extern __shared__ __align__(16) unsigned char smem_all[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int CH = 32 * K;
@@ -409,10 +408,10 @@ struct EvalKernelInfo {
 
 #define TGP_EVAL_INST(K, NW, M, O) {(const void*)eval_kernel<K, NW, M, O>, K, NW, M, O}
 static const EvalKernelInfo kEvalKernels[] = {
+    TGP_EVAL_INST(16, 8, false, false), TGP_EVAL_INST(16, 8, false, true),
     TGP_EVAL_INST(8, 8, false, false), TGP_EVAL_INST(4, 8, false, false),
-    TGP_EVAL_INST(8, 8, true, false),  TGP_EVAL_INST(4, 8, true, false),
-    TGP_EVAL_INST(8, 8, false, true),  TGP_EVAL_INST(4, 8, false, true),
-    TGP_EVAL_INST(8, 8, true, true),   TGP_EVAL_INST(4, 8, true, true),
+    TGP_EVAL_INST(4, 8, true, false),  TGP_EVAL_INST(8, 8, false, true),
+    TGP_EVAL_INST(4, 8, false, true),  TGP_EVAL_INST(4, 8, true, true),
 };
 #undef TGP_EVAL_INST
 

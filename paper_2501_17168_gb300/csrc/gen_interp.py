@@ -182,9 +182,9 @@ class Gen:
     def load_x(self, dst, idx):
         """dst[j] = X tile value of the lane's point j, feature = register idx."""
         self.e(f"mad.lo.u32 r_ad, {idx}, r_xstr, r_xc;")
-        self.e(f"ld.shared.v4.f32 {{{dst(0)}, {dst(1)}, {dst(2)}, {dst(3)}}}, [r_ad];")
-        if self.K == 8:
-            self.e(f"ld.shared.v4.f32 {{{dst(4)}, {dst(5)}, {dst(6)}, {dst(7)}}}, [r_ad+512];")
+        for h in range(self.K // 4):
+            off = f"+{512 * h}" if h else ""
+            self.e(f"ld.shared.v4.f32 {{{dst(4*h)}, {dst(4*h+1)}, {dst(4*h+2)}, {dst(4*h+3)}}}, [r_ad{off}];")
 
     def refetch(self):
         """Skips the second word of a two-word instruction (already in r_nx)."""
@@ -616,7 +616,7 @@ def main():
         "__device__ __forceinline__ unsigned interp_fwd(unsigned pg, unsigned xc, unsigned xstr,",
         "                                               unsigned mo, unsigned sb, float (&acc)[K]);",
     ]
-    for K, modi in ((8, False), (4, False), (8, True), (4, True)):  # the kernels instantiated in eval.cu
+    for K, modi in ((16, False), (8, False), (4, False), (4, True)):  # instantiated in eval.cu
         parts.append(render(K, modi))
     parts.append("}  // namespace tgp")
     open(OUT, "w").write("\n".join(parts) + "\n")

@@ -89,6 +89,8 @@ def test_sr_small_forward_and_mse(orc):
 
 @pytest.mark.parametrize("cfg", [None,
                                  {"points_per_lane": 4},
+                                 {"points_per_lane": 16},
+                                 {"points_per_lane": 16, "trees_per_block": 5, "points_per_tile": 1024},
                                  {"points_per_lane": 8, "trees_per_block": 3, "points_per_tile": 512,
                                   "tiles_per_item": 2},
                                  {"points_per_lane": 4, "trees_per_block": 1, "points_per_tile": 128,
@@ -271,8 +273,7 @@ def test_empty_population_and_points():
     assert m.shape == (0, 1)
 
 
-@pytest.mark.parametrize("cfg", [None, {"points_per_lane": 4},
-                                 {"points_per_lane": 8, "trees_per_block": 3, "points_per_tile": 256}])
+@pytest.mark.parametrize("cfg", [None, {"trees_per_block": 3, "points_per_tile": 256}])
 def test_multi_output_modi_population(orc, cfg):
     prob = W.modi(pop=150, D=2000)
     p = prob.pop
