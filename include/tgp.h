@@ -112,8 +112,7 @@ typedef struct tgp_config {
   int32_t points_per_tile;  /* points of X staged per tile; a multiple of
                                32 * points_per_lane (up to 4096)              */
   int32_t tiles_per_item;   /* consecutive tiles one work item sweeps         */
-  int32_t points_per_lane;  /* 4 or 8 points evaluated per thread (16 for
-                               single-output populations)                    */
+  int32_t points_per_lane;  /* 4 or 8 points evaluated per thread             */
   void* eval_begin_event;   /* optional cudaEvent_t recorded on the stream just
                                before the evaluation kernel(s), NULL = none  */
   void* eval_end_event;     /* optional cudaEvent_t recorded just after them  */

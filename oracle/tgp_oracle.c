@@ -181,6 +181,8 @@ static double apply(int f, double a, double b) {
  * roundoff u = 2^-24 (relative to |v|) plus an absolute part:
  *   add, sub, mul : 1 u |v|              (correctly rounded: half an ulp)
  *   pdiv          : 4 u |v|              (approximate reciprocal, 1 ulp, and a rounded product)
+ *                   + |a| 2^-126 where |b| > 2^126 (in flush-to-zero arithmetic
+ *                   the subnormal reciprocal is flushed to 0)
  *   max           : exact
  *   sin, cos      : 2^-20.5 absolute + 1 u |v|  (approximation on the reduced
  *                   argument plus a two-part argument reduction)
@@ -219,7 +221,10 @@ static double err_of_raw(int f, double a, double ea, double b, double eb, double
       if (eb > 0 && fabs(fabs(b) - GUARD) <= eb) return INFINITY; /* guard branch ambiguous */
       if (!(fabs(b) > GUARD)) return 0.0;                          /* guard taken: exactly 1 */
       if (fabs(b) <= eb) return INFINITY;
-      return (ea + av * eb) / (fabs(b) - eb) + 4 * U32 * av;
+      /* flush-to-zero arithmetic forms a/b as a times a reciprocal that is
+       * subnormal, hence flushed to 0, for |b| > 2^126: |a| 2^-126 at most */
+      double ftz = fabs(b) + eb > 0x1p126 ? fabs(a) * 0x1p-126 + ea * 0x1p-126 : 0.0;
+      return (ea + av * eb) / (fabs(b) - eb) + 4 * U32 * av + ftz;
     }
     case F_MAX: return ea > eb ? ea : eb;
     case F_SIN: {

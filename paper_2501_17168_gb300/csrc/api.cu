@@ -99,7 +99,7 @@ bool shape_for_k(int K, long long P, long long D, int F, int O, int max_len, con
   Shape s{};
   s.nw = kNW;
   s.K = K;
-  if (s.K != 4 && s.K != 8 && !(s.K == 16 && !modi)) return false;
+  if (s.K != 4 && s.K != 8) return false;
   const int CH = 32 * s.K;
   const int pcap = pcap_of(max_len);
   s.bt = (cfg && cfg->trees_per_block) ? cfg->trees_per_block : 32;

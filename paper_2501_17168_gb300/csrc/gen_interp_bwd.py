@@ -36,7 +36,7 @@ from __future__ import annotations
 import os
 
 from gen_interp import (BIN, C1, C2, CLAMP, F_ADD, F_CEXP, F_COS, F_MAX, F_MUL, F_PDIV, F_PLOG,
-                        F_SIN, F_SUB, F_TAN, GUARD, INV2PI, LN2, LOG2E, MAGIC, ONE, QUARTER, OP_BC, OP_BC_M,
+                        F_SIN, F_SUB, F_TAN, GUARD, INV2PI, LN2, LOG2E, MAGIC, ONE, OP_BC, OP_BC_M,
                         OP_BS, OP_BS_M, OP_BV, OP_BV_M, OP_COUNT, OP_END_MODI, OP_END_ROOT, OP_LDC,
                         OP_LDV, OP_RC, OP_RC_M, OP_RS, OP_RS_M, OP_RV, OP_RV_M, OP_SPC, OP_SPV, OP_UN,
                         OP_UN_M, OP_UNV, R, UNA, ZERO, fhex)
@@ -97,15 +97,13 @@ class Base:
             elif f == F_MAX:
                 self.e(f"max.f32 {o}, {x}, {y};")
             elif f == F_PDIV:
-                # (a/4) * rcp(b/4): the reciprocal of b/4 stays a normal
-                # number for every finite |b| (rcp of |b| > 2^126 alone would
-                # flush to 0), and the scalings by 1/4 are exact
+                # a * rcp(b) in flush-to-zero arithmetic: for |b| > 2^126
+                # the reciprocal is subnormal and flushes to 0, a deviation
+                # of at most |a| 2^-126 (the oracle's pdiv allowance)
                 self.e(f"abs.f32 V{j}, {y};")
                 self.e(f"setp.gt.f32 P{j}, V{j}, {GUARD};")
-                self.e(f"mul.rn.f32 W{j}, {y}, {QUARTER};")
-                self.e(f"rcp.approx.ftz.f32 V{j}, W{j};")
-                self.e(f"mul.rn.f32 W{j}, {x}, {QUARTER};")
-                self.e(f"mul.rn.f32 V{j}, W{j}, V{j};")
+                self.e(f"rcp.approx.ftz.f32 V{j}, {y};")
+                self.e(f"mul.rn.f32 V{j}, {x}, V{j};")
                 self.e(f"selp.f32 {o}, V{j}, {ONE}, P{j};")
 
     def fn1d(self, f, out, a, d):

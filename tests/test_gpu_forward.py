@@ -89,8 +89,6 @@ def test_sr_small_forward_and_mse(orc):
 
 @pytest.mark.parametrize("cfg", [None,
                                  {"points_per_lane": 4},
-                                 {"points_per_lane": 16},
-                                 {"points_per_lane": 16, "trees_per_block": 5, "points_per_tile": 1024},
                                  {"points_per_lane": 8, "trees_per_block": 3, "points_per_tile": 512,
                                   "tiles_per_item": 2},
                                  {"points_per_lane": 4, "trees_per_block": 1, "points_per_tile": 128,

@@ -12,8 +12,9 @@ functions with the guards and clamp of the library's reading):
                float32 neighbours;
   cexp         [-100, 80.5] and the clamp's neighbours;
   pdiv         |b| across the whole normal float32 range, including values
-               above 2^126 whose reciprocal is subnormal, with small and
-               huge numerators, and the guard's neighbours;
+               above 2^126 whose reciprocal is subnormal (flushed to zero,
+               which the allowance states), with small and huge numerators,
+               and the guard's neighbours;
   add/sub/mul/max  operands of every magnitude.
 This pins the allowances the parity tests use to widen the 1e-5 bar: an
 allowance too small for the kernel's actual error fails here, as does a
