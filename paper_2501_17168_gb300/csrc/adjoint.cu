@@ -58,6 +58,23 @@ __host__ __device__ inline AdjSmem adj_smem_layout(int K, int nw, bool modi, int
   return L;
 }
 
+// The lane's K points of a chunk, 128 (j / 4) + 4 lane + j % 4 (p points at
+// the lane's first one): K / 4 16-byte shared-memory accesses.
+template <int K>
+__device__ __forceinline__ void ld_lane_pts(float (&v)[K], const float* p) {
+#pragma unroll
+  for (int h = 0; h < K / 4; ++h) {
+    const float4 u = *reinterpret_cast<const float4*>(p + 128 * h);
+    v[4 * h] = u.x; v[4 * h + 1] = u.y; v[4 * h + 2] = u.z; v[4 * h + 3] = u.w;
+  }
+}
+template <int K>
+__device__ __forceinline__ void st_lane_pts(float* p, const float (&v)[K]) {
+#pragma unroll
+  for (int h = 0; h < K / 4; ++h)
+    *reinterpret_cast<float4*>(p + 128 * h) = make_float4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
+}
+
 template <int K, int NW, bool MODI, int CAP>
 __global__ void __launch_bounds__(NW * 32, 3) adjoint_kernel(AdjArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -135,8 +152,10 @@ __global__ void __launch_bounds__(NW * 32, 3) adjoint_kernel(AdjArgs a) {
       for (int ch = 0; ch < nch; ++ch) {
         const int qb = ch * CH + 4 * lane;
         if constexpr (MODI) {
-          for (int o = 0; o < O; ++o)
-            *reinterpret_cast<float4*>(mo_w + o * CH + 4 * lane) = make_float4(0.f, 0.f, 0.f, 0.f);
+          float z[K];
+#pragma unroll
+          for (int j = 0; j < K; ++j) z[j] = 0.0f;
+          for (int o = 0; o < O; ++o) st_lane_pts<K>(mo_w + o * CH + 4 * lane, z);
         }
         __syncwarp();
         float acc[K];
@@ -150,25 +169,25 @@ __global__ void __launch_bounds__(NW * 32, 3) adjoint_kernel(AdjArgs a) {
         for (int o = 0; o < O; ++o) {
           float v[K];
           if (MODI && flag) {
-            const float4 u = *reinterpret_cast<const float4*>(mo_w + o * CH + 4 * lane);
-            v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w;
+            ld_lane_pts<K>(v, mo_w + o * CH + 4 * lane);
           } else {
 #pragma unroll
             for (int j = 0; j < K; ++j) v[j] = o == 0 ? acc[j] : 0.0f;
           }
-          const float4 yy = *reinterpret_cast<const float4*>(ys + o * a.tp + qb);
-          const float yv[4] = {yy.x, yy.y, yy.z, yy.w};
+          float yv[K];
+          ld_lane_pts<K>(yv, ys + o * a.tp + qb);
           const float g2 = g2_w[o];
           float sv[K];
 #pragma unroll
           for (int j = 0; j < K; ++j) {
-            const bool ok = qb + j < np;
+            // the lane's point j of the chunk: 128 (j / 4) + 4 lane + j % 4
+            const bool ok = qb + 128 * (j >> 2) + (j & 3) < np;
             const float r = __fsub_rn(v[j], yv[j]);
             if (ok) sse[o] = fmaf(r, r, sse[o]);
             sv[j] = ok ? __fmul_rn(g2, r) : 0.0f;
           }
           if (MODI && flag) {
-            *reinterpret_cast<float4*>(sd_w + o * CH + 4 * lane) = make_float4(sv[0], sv[1], sv[2], sv[3]);
+            st_lane_pts<K>(sd_w + o * CH + 4 * lane, sv);
           } else if (o == 0) {
 #pragma unroll
             for (int j = 0; j < K; ++j) seed[j] = sv[j];
@@ -200,9 +219,10 @@ __global__ void __launch_bounds__(NW * 32, 3) adjoint_kernel(AdjArgs a) {
     if (a.grad_X) {
       for (int i = tid; i < np * a.F; i += NW * 32) {
         const int q = i / a.F, f = i - (i / a.F) * a.F;
-        // tile layout [f][chunk][j][lane]: point q = chunk*CH + 4*lane + j
-        const int c = q / CH, r = q - c * CH;
-        a.grad_X[(p0 + q) * a.F + f] += gxs[f * XS + c * CH + (r & 3) * 32 + (r >> 2)];
+        // tile layout [f][chunk][j][lane]: point q = chunk*CH + 128*(j/4) +
+        // 4*lane + j%4
+        const int c = q / CH, r = q - c * CH, h = r >> 7, rr = r & 127;
+        a.grad_X[(p0 + q) * a.F + f] += gxs[f * XS + c * CH + (4 * h + (rr & 3)) * 32 + (rr >> 2)];
       }
     }
     __syncthreads();
@@ -234,6 +254,7 @@ struct AdjKernelInfo {
 
 #define TGP_ADJ_INST(K, NW, M, C) {(const void*)adjoint_kernel<K, NW, M, C>, K, NW, C, M}
 static const AdjKernelInfo kAdjKernels[] = {
+    TGP_ADJ_INST(8, 8, false, 128), TGP_ADJ_INST(8, 8, false, 256),
     TGP_ADJ_INST(4, 8, false, 128), TGP_ADJ_INST(4, 8, false, 256), TGP_ADJ_INST(4, 8, false, 1024),
     TGP_ADJ_INST(4, 8, true, 128),  TGP_ADJ_INST(4, 8, true, 256),  TGP_ADJ_INST(4, 8, true, 1024),
 };
