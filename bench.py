@@ -962,8 +962,8 @@ def e1_lines(dev, steps):
     hybrid schedule), its data-parallel shape (one tree per block over
     4,096-point tiles: the analogue of the paper's one-tree-per-launch
     schedule), the library's heuristic and the autotuner's pick, each timed
-    with CUDA events; then, per population, the crossover: the smallest D at
-    which the data-parallel shape is at least as fast."""
+    with CUDA events; then, per population, the data-set sizes at which the
+    data-parallel shape is at least as fast as the population-parallel one."""
     import torch
     from paper_2501_17168_gb300 import api, autotune, workloads as W
     big = W.e1_population(0, max(W.E1_POPS))
@@ -994,10 +994,10 @@ def e1_lines(dev, steps):
                     "ms": ms, "autotuned_shape": best,
                     "node_points_per_s": {k: units / (m / 1e3) for k, m in ms.items()}}
             out.append(line)
-            if P not in cross and ms["data_parallel"] <= ms["population_parallel"]:
-                cross[P] = D
+            if ms["data_parallel"] <= ms["population_parallel"]:
+                cross.setdefault(P, []).append(D)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    out.append({"case": "e1_crossover", "smallest_D_data_parallel_not_slower": cross,
+    out.append({"case": "e1_crossover", "D_where_data_parallel_not_slower": cross,
                 "sm_count": sms, "sm_count_x_128": sms * 128,
                 "paper_threshold_rtx3090": 10_496})
     return out

@@ -254,7 +254,6 @@ struct AdjKernelInfo {
 
 #define TGP_ADJ_INST(K, NW, M, C) {(const void*)adjoint_kernel<K, NW, M, C>, K, NW, C, M}
 static const AdjKernelInfo kAdjKernels[] = {
-    TGP_ADJ_INST(8, 8, false, 128), TGP_ADJ_INST(8, 8, false, 256),
     TGP_ADJ_INST(4, 8, false, 128), TGP_ADJ_INST(4, 8, false, 256), TGP_ADJ_INST(4, 8, false, 1024),
     TGP_ADJ_INST(4, 8, true, 128),  TGP_ADJ_INST(4, 8, true, 256),  TGP_ADJ_INST(4, 8, true, 1024),
 };

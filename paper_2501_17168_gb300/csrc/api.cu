@@ -613,17 +613,11 @@ tgp_status run_backward(const tgp_population* pop, const tgp_data* data, const f
   for (int variant = 0; variant < 2; ++variant) {
     const bool modi = variant == 1;
     if (!modi && O > 1) continue;
-    // 8 points per lane where a kernel for this tree length exists and a
-    // 256-point tile fits (single-output populations), else 4
-    int cap = 0, K = 8;
-    const void* fn = modi ? nullptr : find_adj_kernel(8, nw, modi, pop->max_len, &cap);
-    if (fn && adj_smem_bytes(8, nw, modi, w.pcap, pop->max_len, 256, data->n_features, O) >
-                  (size_t)dv.smem_optin)
-      fn = nullptr;
-    if (!fn) {
-      K = 4;
-      fn = find_adj_kernel(K, nw, modi, pop->max_len, &cap);
-    }
+    // 4 points per lane: at 8 the per-thread tape doubles and the kernel
+    // runs 1.5x slower (156 vs 103 ms on the differentiation workload)
+    int cap = 0;
+    const int K = 4;
+    const void* fn = find_adj_kernel(K, nw, modi, pop->max_len, &cap);
     if (!fn) return TGP_ERR_UNSUPPORTED;
     // A tile (every tree over tp points) is a large unit of work, so prefer
     // enough tiles for several waves of the persistent grid: tiles of 512

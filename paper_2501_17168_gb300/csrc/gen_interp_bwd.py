@@ -750,7 +750,7 @@ def main():
         "                                            unsigned sd, unsigned tend, unsigned lane,",
         "                                            unsigned slot, const float (&seed)[K]);",
     ]
-    for K, modi in ((8, False), (4, False), (4, True)):
+    for K, modi in ((4, False), (4, True)):
         parts.append(render_fwd(K, modi))
         parts.append(render_rev(K, modi))
     parts.append("}  // namespace tgp")
