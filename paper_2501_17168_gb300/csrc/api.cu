@@ -365,6 +365,8 @@ tgp_status launch_eval(Planned* qs, int n, char* ws, unsigned* counters, cudaStr
         a.D = q.data->n_points;
         a.F = q.data->n_features;
         a.ldx = q.data->ldx;
+        a.x_vec4 = (reinterpret_cast<uintptr_t>(q.data->X) & 15) == 0 && q.data->n_features % 4 == 0 &&
+                   q.data->ldx % 4 == 0;
         a.y = q.y;
         a.O = q.O;
         a.out = q.out;

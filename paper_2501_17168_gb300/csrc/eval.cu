@@ -266,19 +266,39 @@ __global__ void __launch_bounds__(NW * 32, K >= 16 ? 2 : 3) eval_kernel(const __
         const long long p0 = tile * a.tp;
         const int np = (int)min((long long)a.tp, a.D - p0);
 
-        // 2. X tile -> xs[f][q] (zero beyond D), targets -> ys[o][q]
+        // 2. X tile -> xs[f][q] (zero beyond D), targets -> ys[o][q]; rows of
+        //    X are read with 16-byte loads when their layout allows
         {
-          const int fw = min(a.F, 32), rows = 32 / fw, rr = lane / fw, ff = lane - rr * fw;
-          for (int f0 = 0; f0 < a.F; f0 += 32) {
-            const int f = f0 + ff;
-            const bool act = rr < rows && f < a.F;
+          if (a.x_vec4) {
+            const int F4 = a.F >> 2;
+            const int fw = min(F4, 32), rows = 32 / fw, rr = lane / fw, ff = lane - rr * fw;
+            for (int f0 = 0; f0 < F4; f0 += 32) {
+              const int f4 = f0 + ff;
+              const bool act = rr < rows && f4 < F4;
+  #pragma unroll 2
+              for (int r0 = warp * rows; r0 < a.tp; r0 += NW * rows) {
+                const int q = r0 + rr;
+                if (act && q < a.tp) {
+                  float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                  if (q < np) v = __ldg(reinterpret_cast<const float4*>(a.X + (p0 + q) * a.ldx) + f4);
+                  float* d = xs + 4 * f4 * XS + q;
+                  d[0] = v.x; d[XS] = v.y; d[2 * XS] = v.z; d[3 * XS] = v.w;
+                }
+              }
+            }
+          } else {
+            const int fw = min(a.F, 32), rows = 32 / fw, rr = lane / fw, ff = lane - rr * fw;
+            for (int f0 = 0; f0 < a.F; f0 += 32) {
+              const int f = f0 + ff;
+              const bool act = rr < rows && f < a.F;
   #pragma unroll 4
-            for (int r0 = warp * rows; r0 < a.tp; r0 += NW * rows) {
-              const int q = r0 + rr;
-              if (act && q < a.tp) {
-                float v = 0.0f;
-                if (q < np) v = __ldg(a.X + (p0 + q) * a.ldx + f);
-                xs[f * XS + q] = v;
+              for (int r0 = warp * rows; r0 < a.tp; r0 += NW * rows) {
+                const int q = r0 + rr;
+                if (act && q < a.tp) {
+                  float v = 0.0f;
+                  if (q < np) v = __ldg(a.X + (p0 + q) * a.ldx + f);
+                  xs[f * XS + q] = v;
+                }
               }
             }
           }

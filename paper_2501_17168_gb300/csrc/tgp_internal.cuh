@@ -136,6 +136,7 @@ struct EvalArgs {
   long long D;
   int F;
   long long ldx;
+  int x_vec4;         // 1: X 16-byte aligned, F and ldx multiples of 4 (float4 rows)
   const float* y;     // [D, O] (MSE mode)
   int O;
   float* out;         // [pop, O, D] (forward mode)
