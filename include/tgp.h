@@ -13,8 +13,9 @@
  *
  * Encoding of one node (the paper leaves the codes open; this is the
  * library's fixed reading):
- *   type  0 variable, 1 constant, 2 unary function, 3 binary function;
- *         18 / 19 are unary / binary Modi function nodes (16 + 2, 16 + 3).
+ *   type  0 variable, 1 constant, 2 unary function, 3 binary function,
+ *         4 ternary function; 18 / 19 / 20 are unary / binary / ternary Modi
+ *         function nodes (16 + 2, 16 + 3, 16 + 4).
  *   value variable: feature index (integer in [0, n_features));
  *         constant: the constant (finite);
  *         function: func_id + 256 * out_index, an integer below 65536, where
@@ -24,11 +25,12 @@
  * Functions (first prefix child = left operand):
  *   0 add, 1 sub, 2 mul, 3 pdiv(a,b) = |b| > 1e-6f ? a/b : 1,
  *   4 max (IEEE fmax), 5 sin, 6 cos, 7 plog(a) = |a| > 1e-6f ? log|a| : 0,
- *   8 cexp(a) = exp(min(a, 80)), 9 tan.
+ *   8 cexp(a) = exp(min(a, 80)), 9 tan, 10 ite(a, b, c) = a > 0 ? b : c (a NaN
+ *   condition selects c; the only ternary function).
  * Outputs: with n_outputs == 1 and no Modi node in the tree the output is the
  * root value; otherwise output k is the sum of the function values of the
  * Modi nodes tagged k (0 if none), and a Modi node hands its parent the value
- * of its rightmost child.
+ * of its rightmost child (c for ite).
  *
  * Conventions for every entry point:
  *   - Pointers marked [device] are CUDA device memory owned by the caller;
@@ -70,15 +72,20 @@ typedef enum {
 enum {
   TGP_TREE_OK = 0,
   TGP_TREE_LEN = 1,     /* size[0] not an integer in [1, max_len]                 */
-  TGP_TREE_TYPE = 2,    /* a type code not in {0,1,2,3,18,19}                    */
+  TGP_TREE_TYPE = 2,    /* a type code not in {0,1,2,3,4,18,19,20}               */
   TGP_TREE_FUNC = 4,    /* function id unknown, arity disagrees with the type,
                            or an output index on a plain function node           */
   TGP_TREE_VAR = 8,     /* variable index not an integer in [0, n_features)      */
   TGP_TREE_MODI = 16,   /* Modi output index not in [0, n_outputs)               */
   TGP_TREE_CONST = 32,  /* constant not finite                                   */
   TGP_TREE_SIZE = 64,   /* subtree sizes disagree with the prefix structure      */
-  TGP_TREE_DEPTH = 128  /* nests deeper than the evaluation registers and stack
-                           hold (never for trees of up to 1024 nodes)           */
+  TGP_TREE_DEPTH = 128, /* nests deeper than the evaluation registers and stack
+                           hold (never for trees of up to 1024 nodes without
+                           ite), or more than 8 ite nodes whose branches are
+                           pending at once (ite nested in ite branches)        */
+  TGP_TREE_NO_ADJOINT = 256 /* tgp_eval_backward only: the tree has an ite node,
+                           which the adjoint does not differentiate; its MSE
+                           and gradients are NaN                               */
 };
 
 /* Library limits. */

@@ -31,8 +31,8 @@ _lock = threading.Lock()
 _lib = None
 
 # restated encoding (Sec. III-A and the readings in tgp_oracle.c)
-VAR, CONST, UFUNC, BFUNC, MODI = 0, 1, 2, 3, 16
-ADD, SUB, MUL, PDIV, MAX, SIN, COS, PLOG, CEXP, TAN = range(10)
+VAR, CONST, UFUNC, BFUNC, TFUNC, MODI = 0, 1, 2, 3, 4, 16
+ADD, SUB, MUL, PDIV, MAX, SIN, COS, PLOG, CEXP, TAN, ITE = range(11)
 
 ST_LEN, ST_TYPE, ST_FUNC, ST_VAR, ST_MODI, ST_CONST, ST_SIZE = 1, 2, 4, 8, 16, 32, 64
 
@@ -71,6 +71,8 @@ def _load():
             lib.orc_grad_bound.restype = None
             lib.orc_apply.argtypes = [I, D, D]
             lib.orc_apply.restype = D
+            lib.orc_apply3.argtypes = [I, D, D, D]
+            lib.orc_apply3.restype = D
             _lib = lib
     return _lib
 

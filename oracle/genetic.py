@@ -44,7 +44,7 @@ import numpy as np
 from . import evaluate as _evaluate
 
 # restated encoding (Sec. III-A): arity of each node type
-_ARITY = {0: 0, 1: 0, 2: 1, 3: 2, 18: 1, 19: 2}
+_ARITY = {0: 0, 1: 0, 2: 1, 3: 2, 4: 3, 18: 1, 19: 2, 20: 3}
 
 # per-child status of an exchange (the library's reading, restated)
 DONE, TOO_LARGE, SKIPPED, BAD_INDEX, BAD_TREE = 1, 0, 2, -1, -2

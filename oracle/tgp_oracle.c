@@ -34,7 +34,10 @@
  *           function -> func_id + 256 * output_index (output_index only on
  *           Modi nodes, 0 otherwise); an integer below 65536.
  *   func  : 0 add, 1 sub, 2 mul, 3 protected div, 4 max (binary);
- *           5 sin, 6 cos, 7 protected log, 8 clamped exp, 9 tan (unary).
+ *           5 sin, 6 cos, 7 protected log, 8 clamped exp, 9 tan (unary);
+ *           10 ite (ternary; type 4, 20 on a Modi node).
+ *   ite(a, b, c) = a > 0 ? b : c (a NaN condition selects c): the paper's
+ *   encoding admits any arity fixed by (type, value), Sec. III-A.
  *   The first prefix child is the left operand: [sub, a, b] = a - b.
  *   pdiv(a,b) = |b| > 1e-6f ? a/b : 1 ;  plog(a) = |a| > 1e-6f ? log|a| : 0 ;
  *   cexp(a)   = exp(min(a, 80)) ; max = IEEE fmax (a NaN operand yields the
@@ -59,8 +62,8 @@
 #include <pthread.h>
 
 /* ---- encoding restated from the paper's Sec. III-A and the readings above ---- */
-enum { T_VAR = 0, T_CONST = 1, T_UFUNC = 2, T_BFUNC = 3, T_MODI = 16 };
-enum { F_ADD = 0, F_SUB, F_MUL, F_PDIV, F_MAX, F_SIN, F_COS, F_PLOG, F_CEXP, F_TAN, F_COUNT };
+enum { T_VAR = 0, T_CONST = 1, T_UFUNC = 2, T_BFUNC = 3, T_TFUNC = 4, T_MODI = 16 };
+enum { F_ADD = 0, F_SUB, F_MUL, F_PDIV, F_MAX, F_SIN, F_COS, F_PLOG, F_CEXP, F_TAN, F_ITE, F_COUNT };
 
 /* validator status bits (restated; the library defines its own) */
 enum {
@@ -78,7 +81,7 @@ static const double GUARD = (double)1e-6f;
 static const double EXP_CLAMP = 80.0;
 static const double U32 = 5.9604644775390625e-08; /* 2^-24 */
 
-static int arity_of(int f) { return f <= F_MAX ? 2 : 1; }
+static int arity_of(int f) { return f <= F_MAX ? 2 : f == F_ITE ? 3 : 1; }
 
 static int is_int(double v) { return isfinite(v) && v == floor(v); }
 
@@ -95,7 +98,7 @@ static int parse(const tree_t* t, int i, int* true_size) {
   if (i >= t->len) return -1;
   int ty = (int)t->type[i] & ~T_MODI;
   int nxt = i + 1;
-  if (ty == T_UFUNC || ty == T_BFUNC) {
+  if (ty == T_UFUNC || ty == T_BFUNC || ty == T_TFUNC) {
     int f = ((int)t->val[i]) % 256;
     for (int c = 0; c < arity_of(f); ++c) {
       nxt = parse(t, nxt, true_size);
@@ -120,7 +123,10 @@ int orc_validate_one(const float* type, const float* val, const float* size,
     int ty = (is_int(tv) && tv >= 0 && tv < 64) ? (int)tv : -1;
     int base = ty >= 0 ? (ty & ~T_MODI) : -1;
     int modi = ty >= 0 && (ty & T_MODI);
-    if (!(ty == 0 || ty == 1 || ty == 2 || ty == 3 || ty == 18 || ty == 19)) { st |= ST_TYPE; continue; }
+    if (!(ty == 0 || ty == 1 || ty == 2 || ty == 3 || ty == 4 || ty == 18 || ty == 19 || ty == 20)) {
+      st |= ST_TYPE;
+      continue;
+    }
     if (base == T_VAR) {
       if (!is_int(vv) || vv < 0 || vv >= n_features) st |= ST_VAR;
     } else if (base == T_CONST) {
@@ -130,7 +136,8 @@ int orc_validate_one(const float* type, const float* val, const float* size,
       long iv = (long)vv;
       int f = (int)(iv % 256);
       long o = iv / 256;
-      if (f >= F_COUNT || arity_of(f) != (base == T_UFUNC ? 1 : 2)) st |= ST_FUNC;
+      /* the type names the arity: 2 unary, 3 binary, 4 ternary */
+      if (f >= F_COUNT || arity_of(f) != base - 1) st |= ST_FUNC;
       if (modi) { if (o >= n_outputs) st |= ST_MODI; }
       else if (o != 0) st |= ST_FUNC;
     }
@@ -159,7 +166,28 @@ typedef struct {
   double* fv;     /* function value (differs from v on Modi)     */
   int* c2;        /* index of the second child, per binary node  */
   double* ev;     /* FP32 error bound of v, per node (or NULL)   */
+  int* c3;        /* index of the third child, per ternary node  */
+  /* per output: sum of |contribution| and number of contributions, for the
+   * rounding of a Modi sum taken in any order (bound mode only) */
+  double msum[64];
+  int mcnt[64];
 } ctx_t;
+
+/* The bound of a Modi output summed in FP32 in any order: the
+ * contributions' own bounds plus (m - 1) u times the sum of their
+ * magnitudes (recursive summation of m terms). */
+static void finish_outputs(ctx_t* c, int O) {
+  if (!c->want_err || !c->eout) return;
+  for (int k = 0; k < O && k < 64; ++k) {
+    if (c->mcnt[k] > 1) c->eout[k] += (double)(c->mcnt[k] - 1) * U32 * c->msum[k];
+    if (!isfinite(c->out[k]) || !(c->eout[k] < INFINITY) || fabs(c->out[k]) + c->eout[k] > FLT_MAX)
+      c->eout[k] = INFINITY;
+  }
+}
+
+static double apply3(int f, double a, double b, double c) {
+  return f == F_ITE ? (a > 0 ? b : c) : NAN;
+}
 
 static double apply(int f, double a, double b) {
   switch (f) {
@@ -275,28 +303,46 @@ static double eval_node(ctx_t* c, int i, int* next, double* err) {
     long iv = (long)t->val[i];
     int f = (int)(iv % 256);
     int o = (int)(iv / 256);
-    double a, b = 0.0, ea = 0.0, eb = 0.0;
-    int n1, n2;
+    double a, b = 0.0, ea = 0.0, eb = 0.0, c3v = 0.0, ec = 0.0;
+    int n1, n2, n3;
     a = eval_node(c, i + 1, &n1, &ea);
     double right = a, eright = ea; /* rightmost child's value */
-    if (arity_of(f) == 2) {
+    if (arity_of(f) >= 2) {
       if (c->c2) c->c2[i] = n1;
       b = eval_node(c, n1, &n2, &eb);
       right = b; eright = eb;
     } else {
       n2 = n1;
     }
-    *next = n2;
-    double fv = apply(f, a, b);
-    double fe = c->want_err ? err_of(f, a, ea, b, eb, fv) : 0.0;
+    if (arity_of(f) == 3) {
+      if (c->c3) c->c3[i] = n2;
+      c3v = eval_node(c, n2, &n3, &ec);
+      right = c3v; eright = ec;
+    } else {
+      n3 = n2;
+    }
+    *next = n3;
+    double fv, fe = 0.0;
+    if (f == F_ITE) {
+      fv = apply3(f, a, b, c3v);
+      /* the chosen branch's error, or anything when the sign of a is
+       * undecided by its error (the FP32 path may take the other branch) */
+      if (c->want_err) fe = (ea > 0 && fabs(a) <= ea) || !(ea < INFINITY) ? INFINITY : (a > 0 ? eb : ec);
+    } else {
+      fv = apply(f, a, b);
+      fe = c->want_err ? err_of(f, a, ea, b, eb, fv) : 0.0;
+    }
     if (c->want_err && (!isfinite(fv) || fabs(fv) + fe > FLT_MAX)) fe = INFINITY;
     if (ty & T_MODI) {
       /* Sec. IV-C: the function value is summed into output o and the parent
        * sees the rightmost child's value. */
       c->out[o] += fv;
       if (c->want_err) {
-        c->eout[o] += fe + U32 * fabs(c->out[o]);
-        if (!isfinite(c->out[o]) || fabs(c->out[o]) + c->eout[o] > FLT_MAX) c->eout[o] = INFINITY;
+        c->eout[o] += fe;
+        if (o < 64) {
+          c->msum[o] += fabs(fv);
+          c->mcnt[o] += 1;
+        }
       }
       v = right;
       e = eright;
@@ -321,13 +367,15 @@ static int tree_has_modi(const tree_t* t) {
 static void eval_point(const tree_t* t, int has_modi, const float* x, int O,
                        double* out, double* eout, int want_err) {
   for (int k = 0; k < O; ++k) { out[k] = 0.0; if (eout) eout[k] = 0.0; }
-  ctx_t c = {t, x, out, eout, want_err, NULL, NULL, NULL, NULL};
+  ctx_t c = {t, x, out, eout, want_err, NULL, NULL, NULL, NULL, NULL};
   int nx;
   double e;
   double r = eval_node(&c, 0, &nx, &e);
   if (!has_modi && O == 1) {
     out[0] = r;
     if (eout) eout[0] = e;
+  } else {
+    finish_outputs(&c, O);
   }
 }
 
@@ -445,17 +493,22 @@ static void backprop(ctx_t* c, int i, double adj, const double* seed,
   int f = (int)(iv % 256);
   int o = (int)(iv / 256);
   int ia = i + 1;
-  int ib = arity_of(f) == 2 ? c->c2[i] : -1;
+  int ib = arity_of(f) >= 2 ? c->c2[i] : -1;
+  int ic = arity_of(f) == 3 ? c->c3[i] : -1;
   double a = c->v[ia], b = ib >= 0 ? c->v[ib] : 0.0;
   /* adjoint of the function value: the parent's on a plain node, the
    * output's seed on a Modi node (whose parent sees the rightmost child) */
   double af = (ty & T_MODI) ? seed[o] : adj;
-  double pass_b = 0.0, pass_a = 0.0;
+  double pass_b = 0.0, pass_a = 0.0, pass_c = 0.0;
   if (ty & T_MODI) {
-    if (ib >= 0) pass_b = adj; else pass_a = adj;
+    if (ic >= 0) pass_c = adj; else if (ib >= 0) pass_b = adj; else pass_a = adj;
   }
-  double da = 0.0, db = 0.0;
+  double da = 0.0, db = 0.0, dc = 0.0;
   switch (f) {
+    case F_ITE:
+      /* the adjoint goes to the branch ite chose; the condition gets none */
+      if (a > 0) db = 1; else dc = 1;
+      break;
     case F_ADD: da = 1; db = 1; break;
     case F_SUB: da = 1; db = -1; break;
     case F_MUL: da = b; db = a; break;
@@ -479,6 +532,10 @@ static void backprop(ctx_t* c, int i, double adj, const double* seed,
   if (ib >= 0) {
     double gb = pass_b + (db != 0.0 ? af * db : 0.0);
     backprop(c, ib, gb, seed, gval, gx);
+  }
+  if (ic >= 0) {
+    double gc = pass_c + (dc != 0.0 ? af * dc : 0.0);
+    backprop(c, ic, gc, seed, gval, gx);
   }
 }
 
@@ -570,17 +627,29 @@ static void backprop_err(ctx_t* c, int i, double adj, double eadj, const double*
   int f = (int)(iv % 256);
   int o = (int)(iv / 256);
   int ia = i + 1;
-  int ib = arity_of(f) == 2 ? c->c2[i] : -1;
+  int ib = arity_of(f) >= 2 ? c->c2[i] : -1;
+  int ic = arity_of(f) == 3 ? c->c3[i] : -1;
   double a = c->v[ia], ea = c->ev[ia];
   double b = ib >= 0 ? c->v[ib] : 0.0, eb = ib >= 0 ? c->ev[ib] : 0.0;
   double af = (ty & T_MODI) ? seed[o] : adj;
   double eaf = (ty & T_MODI) ? eseed[o] : eadj;
-  double pass_a = 0.0, pass_b = 0.0, epass_a = 0.0, epass_b = 0.0;
+  double pass_a = 0.0, pass_b = 0.0, pass_c = 0.0, epass_a = 0.0, epass_b = 0.0, epass_c = 0.0;
   if (ty & T_MODI) {
-    if (ib >= 0) { pass_b = adj; epass_b = eadj; } else { pass_a = adj; epass_a = eadj; }
+    if (ic >= 0) { pass_c = adj; epass_c = eadj; }
+    else if (ib >= 0) { pass_b = adj; epass_b = eadj; }
+    else { pass_a = adj; epass_a = eadj; }
   }
-  double da, eda, db, edb;
-  dlocal(f, a, ea, b, eb, &da, &eda, &db, &edb);
+  double da, eda, db, edb, dc = 0.0, edc = 0.0;
+  if (f == F_ITE) {
+    /* the adjoint goes to the chosen branch; an undecided sign of the
+     * condition may send it to the other one */
+    da = eda = 0.0;
+    db = a > 0 ? 1.0 : 0.0;
+    dc = a > 0 ? 0.0 : 1.0;
+    edb = edc = (ea > 0 && fabs(a) <= ea) ? INFINITY : 0.0;
+  } else {
+    dlocal(f, a, ea, b, eb, &da, &eda, &db, &edb);
+  }
   /* one FP32 product (and one sum on a Modi node's pass-through) per child */
   /* a zero local derivative contributes nothing (as in backprop), but its
    * bound still counts: the FP32 path may see a non-zero one */
@@ -596,6 +665,13 @@ static void backprop_err(ctx_t* c, int i, double adj, double eadj, const double*
                  U32 * fabs(gb);
     if (!(egb < INFINITY) || fabs(gb) + egb > FLT_MAX) egb = INFINITY;
     backprop_err(c, ib, gb, egb, seed, eseed, gval, egval, sgval, gx, egx, sgx);
+  }
+  if (ic >= 0) {
+    double gc = pass_c + (dc != 0.0 ? af * dc : 0.0);
+    double egc = epass_c + fabs(af) * edc + eaf * fabs(dc) + eaf * edc + U32 * fabs(af * dc) +
+                 U32 * fabs(gc);
+    if (!(egc < INFINITY) || fabs(gc) + egc > FLT_MAX) egc = INFINITY;
+    backprop_err(c, ic, gc, egc, seed, eseed, gval, egval, sgval, gx, egx, sgx);
   }
 }
 
@@ -620,7 +696,8 @@ static void do_grad_tree(job_t* j, long p, double* gx_priv, double* egx_priv) {
   double* fv = v + len;
   double* ev = v + 2 * (size_t)len;
   double* sgval = v + 3 * (size_t)len;
-  int* c2 = (int*)malloc(sizeof(int) * (size_t)len);
+  int* c2 = (int*)malloc(sizeof(int) * (size_t)len * 2);
+  int* c3 = c2 + len;
   double* buf = (double*)calloc((size_t)O * 5, sizeof(double));
   double *out = buf, *acc = buf + O, *seed = buf + 2 * O, *eout = buf + 3 * O, *eseed = buf + 4 * O;
   double* egval = we ? j->egrad_val + p * j->ld : NULL;
@@ -632,11 +709,12 @@ static void do_grad_tree(job_t* j, long p, double* gx_priv, double* egx_priv) {
   double inv_d = 1.0 / (double)j->D;
   for (long d = 0; d < j->D; ++d) {
     for (int k = 0; k < O; ++k) { out[k] = 0.0; eout[k] = 0.0; }
-    ctx_t c = {&t, j->X + d * j->ldx, out, we ? eout : NULL, we, v, fv, c2, we ? ev : NULL};
+    ctx_t c = {&t, j->X + d * j->ldx, out, we ? eout : NULL, we, v, fv, c2, we ? ev : NULL, c3};
     int nx;
     double e;
     double r0 = eval_node(&c, 0, &nx, &e);
     if (!hm && O == 1) { out[0] = r0; eout[0] = e; }
+    else finish_outputs(&c, O);
     for (int k = 0; k < O; ++k) {
       double r = out[k] - (double)j->y[d * j->ldy + k];
       acc[k] += r * r;
@@ -799,3 +877,4 @@ void orc_grad(const float* type, const float* val, const float* size, long pop, 
 
 /* Single-function evaluation in FP64 (used to pin the function table). */
 double orc_apply(int f, double a, double b) { return apply(f, a, b); }
+double orc_apply3(int f, double a, double b, double c) { return apply3(f, a, b, c); }

@@ -18,6 +18,7 @@ TGP_OK, TGP_ERR_INVALID_ARG, TGP_ERR_INVALID_TREE, TGP_ERR_WORKSPACE, TGP_ERR_CU
     TGP_ERR_TIMEOUT, TGP_ERR_UNSUPPORTED = range(7)
 TREE_LEN, TREE_TYPE, TREE_FUNC, TREE_VAR, TREE_MODI, TREE_CONST, TREE_SIZE, TREE_DEPTH = \
     1, 2, 4, 8, 16, 32, 64, 128
+TREE_NO_ADJOINT = 256
 MAX_LEN, MAX_OUTPUTS, MAX_FEATURES = 1024, 16, 256
 NOALLOC_WS_BYTES = 32 << 20
 PICK_NODES, PICK_RANDOM, PICK_HOIST = 0, 1, 2

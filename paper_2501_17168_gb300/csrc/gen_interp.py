@@ -56,9 +56,12 @@ OUT = os.path.join(HERE, "interp_fwd.cuh")
 OUT_ISA = os.path.join(HERE, "isa_fwd.cuh")
 
 R = 8
-F_ADD, F_SUB, F_MUL, F_PDIV, F_MAX, F_SIN, F_COS, F_PLOG, F_CEXP, F_TAN = range(10)
-BIN = [F_ADD, F_SUB, F_MUL, F_PDIV, F_MAX]
+F_ADD, F_SUB, F_MUL, F_PDIV, F_MAX, F_SIN, F_COS, F_PLOG, F_CEXP, F_TAN, F_ITE = range(11)
+BIN = [F_ADD, F_SUB, F_MUL, F_PDIV, F_MAX]   # binary functions of the adjoint set
 UNA = [F_SIN, F_COS, F_PLOG, F_CEXP, F_TAN]
+# binary forms of the forward set: the binary functions, then ite's branch
+# selection (its condition is pushed by a CD form before the branches)
+FBIN = BIN + [F_ITE]
 
 # opcode layout (must match enum Op in tgp_internal.cuh)
 OP_END_ROOT, OP_END_MODI, OP_LDV, OP_LDC = 0, 1, 2, 3
@@ -87,31 +90,39 @@ MAGIC = fhex(12582912.0)      # 1.5 * 2^23: x + MAGIC - MAGIC = rint(x) for |x| 
 # ------------------------------------------------------------------ forward ISA
 NREG = 3          # nesting levels held in registers
 MAXS = 6          # local-memory stack entries: trees of <= 1024 nodes need <= 9 levels
-NC = [F_SUB, F_PDIV]   # non-commutative binary functions (max is symmetric in PTX)
+NC = [F_SUB, F_PDIV, F_ITE]   # non-commutative binary forms (max is symmetric in PTX)
+NB = len(FBIN)
+
+
+def bi(f):
+    """Sub-index of a binary form's function."""
+    return FBIN.index(f)
 
 # (name, number of sub-forms); level forms come first, then memory forms
 LEVEL_FORMS = [
     ("LDV", 1), ("LDC", 1),                       # G[d] = x[v] / c (only a lone leaf)
     ("UN", 5), ("UNV", 5), ("UNC", 5),            # G[d] = f(G[d]) / f(x[v]) / f(c)
-    ("BV", 5), ("BC", 5),                         # G[d] = f(G[d], x[v]) / f(G[d], c)
-    ("RV", 2), ("RC", 2),                         # G[d] = f(x[v], G[d]) / f(c, G[d])
-    ("VV", 5),                                    # G[d] = f(x[v1], x[v2]), y = v1 | v2 << 16
-    ("VC", 5), ("CV", 2),                         # f(x[v], c) / f(c, x[v]); second word .x = v
-    ("CC", 5),                                    # f(c1, c2); second word .x = bits of c2
-    ("BS", 5), ("RS", 2),                         # G[d] = f(G[d], G[d+1]) / f(G[d+1], G[d])
+    ("BV", NB), ("BC", NB),                       # G[d] = f(G[d], x[v]) / f(G[d], c)
+    ("RV", 3), ("RC", 3),                         # G[d] = f(x[v], G[d]) / f(c, G[d])
+    ("VV", NB),                                   # G[d] = f(x[v1], x[v2]), y = v1 | v2 << 16
+    ("VC", NB), ("CV", 3),                        # f(x[v], c) / f(c, x[v]); second word .x = v
+    ("CC", NB),                                   # f(c1, c2); second word .x = bits of c2
+    ("BS", NB), ("RS", 3),                        # G[d] = f(G[d], G[d+1]) / f(G[d+1], G[d])
     ("UN_M", 5), ("UNV_M", 5), ("UNC_M", 5),      # Modi: out += f(.), G[d] = the operand
-    ("BV_M", 5), ("BC_M", 5), ("RV_M", 5), ("RC_M", 5),
-    ("BS_M", 5), ("RS_M", 5),
+    ("BV_M", NB), ("BC_M", NB), ("RV_M", NB), ("RC_M", NB),
+    ("BS_M", NB), ("RS_M", NB),
+    ("CD", 1), ("CDV", 1), ("CDC", 1),            # push the sign bits of G[d] / x[v] / c > 0
 ]
 NSM = 1           # memory-stack entries held in shared memory (the deeper ones in local memory)
 MEM_FORMS = [
     ("SAVE", 1),                                  # push G[NREG-1] (local memory)
-    ("MS", 5), ("SM", 2),                         # pop m: G = f(m, G) / f(G, m)  (G = G[NREG-1])
-    ("MS_M", 5), ("SM_M", 5),
+    ("MS", NB), ("SM", 3),                        # pop m: G = f(m, G) / f(G, m)  (G = G[NREG-1])
+    ("MS_M", NB), ("SM_M", NB),
     ("SAVES", NSM),                               # the same for entry s < NSM in shared memory
-    ("MSS", 5 * NSM), ("SMS", 2 * NSM),           #   (sub = f * NSM + s)
-    ("MSS_M", 5 * NSM), ("SMS_M", 5 * NSM),
+    ("MSS", NB * NSM), ("SMS", 3 * NSM),          #   (sub = f * NSM + s)
+    ("MSS_M", NB * NSM), ("SMS_M", NB * NSM),
 ]
+MAXC = 8          # pending ite conditions: 64 condition bits, 8 points per lane
 
 
 def isa_layout():
@@ -154,6 +165,18 @@ def layout_key(op):
     else:
         sub, lvl = divmod(op - base, NREG)
     cold = name in ("UN", "UNV", "UNC", "UN_M", "UNV_M", "UNC_M") and UNA[sub] == F_TAN
+    # ite's forms are rare (and absent from most function sets): kept cold
+    cold |= name in ("CD", "CDV", "CDC")
+    binf = {"BV", "BC", "VV", "VC", "CC", "BS", "BV_M", "BC_M", "RV_M", "RC_M", "BS_M", "RS_M",
+            "MS", "MS_M", "SM_M"}
+    if name in binf:
+        cold |= sub == bi(F_ITE)
+    if name in ("MSS", "MSS_M", "SMS_M"):
+        cold |= sub // NSM == bi(F_ITE)
+    if name in ("RV", "RC", "CV", "RS", "SM"):
+        cold |= sub == NC.index(F_ITE)
+    if name == "SMS":
+        cold |= sub // NSM == NC.index(F_ITE)
     return (1 if cold else 0, lvl, order, sub)
 
 
@@ -211,6 +234,15 @@ class Gen:
 
     # ---- function bodies: out[j] = f(a[j], b[j]); a, b, out are name functions
     def fn2(self, f, out, a, b):
+        if f == F_ITE:
+            # pop the condition bits of the K points: out = cond ? a : b
+            self.e("cvt.u32.u64 r_c, r_cs;")
+            for j in range(self.K):
+                self.e(f"and.b32 r_ct, r_c, {1 << j};")
+                self.e(f"setp.ne.u32 P{j}, r_ct, 0;")
+                self.e(f"selp.f32 {out(j)}, {a(j)}, {b(j)}, P{j};")
+            self.e(f"shr.b64 r_cs, r_cs, {self.K};")
+            return
         for j in range(self.K):
             o, x, y = out(j), a(j), b(j)
             if f == F_ADD:
@@ -278,6 +310,23 @@ class Gen:
                 self.e(f"add.rn.f32 {regs[q]}, {regs[q]}, {src(4 * h + q)};")
             self.e(f"st.shared.v4.f32 [r_ma{off}], {{{', '.join(regs)}}};")
 
+    def cond(self, src, scalar=False):
+        """Pushes the K sign bits (value > 0; NaN is not) of src onto the
+        condition stack r_cs (K bits per entry, the newest in the low bits)."""
+        K = self.K
+        if scalar:
+            self.e(f"setp.gt.f32 P0, {src(0)}, 0f00000000;")
+            self.e(f"selp.u32 r_cb, {(1 << K) - 1}, 0, P0;")
+        else:
+            self.e("mov.u32 r_cb, 0;")
+            for j in range(K):
+                self.e(f"setp.gt.f32 P{j}, {src(j)}, 0f00000000;")
+                self.e(f"selp.u32 r_ct, {1 << j}, 0, P{j};")
+                self.e("or.b32 r_cb, r_cb, r_ct;")
+        self.e("cvt.u64.u32 r_cb64, r_cb;")
+        self.e(f"shl.b64 r_cs, r_cs, {K};")
+        self.e("or.b64 r_cs, r_cs, r_cb64;")
+
     def case(self, op, body, then=None):
         """Label C<op>, its body, then back to the dispatch (or on to `then`:
         another case's opcode or a body label)."""
@@ -316,7 +365,9 @@ class Gen:
         self.e(".reg .f32 " + ", ".join(G(d)(j) for d in range(NREG) for j in range(K)) + ";")
         self.e(".reg .pred " + ", ".join(f"P{j}" for j in range(K)) + ";")
         self.e(".reg .u32 r_ptr, r_ix, r_iy, r_nx, r_ny, r_op, r_ad, r_xc, r_xstr, r_mo, r_moo, "
-               "r_ma, r_flag, r_t, r_sp, r_sb;")
+               "r_ma, r_flag, r_t, r_sp, r_sb, r_c, r_cb, r_ct;")
+        self.e(".reg .b64 r_cs, r_cb64;")
+        self.e("mov.b64 r_cs, 0;")
         self.e(f".local .align 16 .b8 gm[{MAXS * K * 4}];")
         self.e("mov.u32 r_sp, gm;")
         self.e("mov.u32 r_sb, %{sb};")
@@ -350,6 +401,11 @@ class Gen:
             Gd = G(d)
             self.case(fx("LDV", 0, d), lambda: self.load_x(Gd, "r_iy"))
             self.case(fx("LDC", 0, d), lambda: self.movs(Gd, cv))
+            # ite's condition: G[d] holds nothing live until the branches, so
+            # a leaf condition is loaded there
+            self.case(fx("CD", 0, d), lambda: self.cond(Gd))
+            self.case(fx("CDV", 0, d), lambda: (self.load_x(Gd, "r_iy"), self.cond(Gd)))
+            self.case(fx("CDC", 0, d), lambda: self.cond(cv, scalar=True))
             for u, f in enumerate(UNA):
                 un = fx("UN", u, d)
                 self.case(un, lambda f=f: self.fn1(f, Gd, Gd))
@@ -359,10 +415,10 @@ class Gen:
             # runs, so below the top level a leaf operand is loaded into
             # G[d+1] and the slot-combining body of BS/RS is reused
             Gn = G(d + 1) if d < top else L
-            for f in BIN:
-                bv, bc = fx("BV", f, d), fx("BC", f, d)
+            for f in FBIN:
+                bv, bc = fx("BV", bi(f), d), fx("BC", bi(f), d)
                 if d < top:
-                    self.case(bv, lambda: self.load_x(Gn, "r_iy"), then=fx("BS", f, d))
+                    self.case(bv, lambda: self.load_x(Gn, "r_iy"), then=fx("BS", bi(f), d))
                 else:
                     self.case(bv, lambda f=f: (self.load_x(L, "r_iy"), self.fn2(f, Gd, Gd, L)))
                 self.case(bc, lambda f=f: self.fn2(f, Gd, Gd, cv))
@@ -374,22 +430,22 @@ class Gen:
                     if d < top:
                         self.load_x(Gn, "r_iy")
 
-                self.case(fx("VV", f, d), vv, then=fx("BS", f, d) if d < top else bv)
+                self.case(fx("VV", bi(f), d), vv, then=fx("BS", bi(f), d) if d < top else bv)
 
                 def vc():
                     self.load_x(Gd, "r_nx")
                     self.refetch()
 
-                self.case(fx("VC", f, d), vc, then=bc)
+                self.case(fx("VC", bi(f), d), vc, then=bc)
 
                 def cc(f=f):
                     self.e("mov.b32 c2v, r_nx;")
                     self.refetch()
                     self.fn2(f, Gd, cv, c2)
 
-                self.case(fx("CC", f, d), cc)
+                self.case(fx("CC", bi(f), d), cc)
                 if d < top:
-                    self.case(fx("BS", f, d), lambda f=f: self.fn2(f, Gd, Gd, G(d + 1)))
+                    self.case(fx("BS", bi(f), d), lambda f=f: self.fn2(f, Gd, Gd, G(d + 1)))
             for i, f in enumerate(NC):
                 rc = fx("RC", i, d)
                 if d < top:
@@ -412,7 +468,7 @@ class Gen:
                 self.case(unm, lambda f=f: (self.fn1(f, T, Gd), self.modi_add(T)))
                 self.case(fx("UNV_M", u, d), lambda: self.load_x(Gd, "r_iy"), then=unm)
                 self.case(fx("UNC_M", u, d), lambda: self.movs(Gd, cv), then=unm)
-            for f in BIN:
+            for f in FBIN:
                 def bvm(f=f):
                     self.load_x(L, "r_iy")
                     self.fn2(f, T, Gd, L)
@@ -435,15 +491,15 @@ class Gen:
 
                 if d < top:
                     # the leaf operand goes to G[d+1]; BS_M/RS_M do the rest
-                    self.case(fx("BV_M", f, d), lambda: self.load_x(Gn, "r_iy"), then=fx("BS_M", f, d))
-                    self.case(fx("BC_M", f, d), lambda: self.movs(Gn, cv), then=fx("BS_M", f, d))
-                    self.case(fx("RV_M", f, d), lambda: self.load_x(Gn, "r_iy"), then=fx("RS_M", f, d))
-                    self.case(fx("RC_M", f, d), lambda: self.movs(Gn, cv), then=fx("RS_M", f, d))
+                    self.case(fx("BV_M", bi(f), d), lambda: self.load_x(Gn, "r_iy"), then=fx("BS_M", bi(f), d))
+                    self.case(fx("BC_M", bi(f), d), lambda: self.movs(Gn, cv), then=fx("BS_M", bi(f), d))
+                    self.case(fx("RV_M", bi(f), d), lambda: self.load_x(Gn, "r_iy"), then=fx("RS_M", bi(f), d))
+                    self.case(fx("RC_M", bi(f), d), lambda: self.movs(Gn, cv), then=fx("RS_M", bi(f), d))
                 else:
-                    self.case(fx("BV_M", f, d), bvm)
-                    self.case(fx("BC_M", f, d), bcm)
-                    self.case(fx("RV_M", f, d), rvm)
-                    self.case(fx("RC_M", f, d), rcm)
+                    self.case(fx("BV_M", bi(f), d), bvm)
+                    self.case(fx("BC_M", bi(f), d), bcm)
+                    self.case(fx("RV_M", bi(f), d), rvm)
+                    self.case(fx("RC_M", bi(f), d), rcm)
                 if d < top:
                     def bsm(f=f):
                         self.fn2(f, T, Gd, G(d + 1))
@@ -454,8 +510,8 @@ class Gen:
                         self.fn2(f, T, G(d + 1), Gd)
                         self.modi_add(T)
 
-                    self.case(fx("BS_M", f, d), bsm)
-                    self.case(fx("RS_M", f, d), rsm)
+                    self.case(fx("BS_M", bi(f), d), bsm)
+                    self.case(fx("RS_M", bi(f), d), rsm)
 
         # memory stack: entry s < NSM in the warp's shared-memory rows, deeper
         # entries in local memory; a pop loads the entry into L and goes on
@@ -483,18 +539,18 @@ class Gen:
         self.case(fx("SAVE", 0, 0), lambda: self.mem_push(Gt))
         for q in range(NSM):
             self.case(fx("SAVES", q, 0), lambda q=q: sm_push(q))
-        for f in BIN:
+        for f in FBIN:
             self.body(f"MSB{f}", lambda f=f: self.fn2(f, Gt, L, Gt))
-            self.case(fx("MS", f, 0), lambda: self.mem_pop(L), then=f"MSB{f}")
+            self.case(fx("MS", bi(f), 0), lambda: self.mem_pop(L), then=f"MSB{f}")
             for q in range(NSM):
-                self.case(fx("MSS", f * NSM + q, 0), lambda q=q: sm_pop(q), then=f"MSB{f}")
+                self.case(fx("MSS", bi(f) * NSM + q, 0), lambda q=q: sm_pop(q), then=f"MSB{f}")
         for i, f in enumerate(NC):
             self.body(f"SMB{i}", lambda f=f: self.fn2(f, Gt, Gt, L))
             self.case(fx("SM", i, 0), lambda: self.mem_pop(L), then=f"SMB{i}")
             for q in range(NSM):
                 self.case(fx("SMS", i * NSM + q, 0), lambda q=q: sm_pop(q), then=f"SMB{i}")
         if self.modi:
-            for f in BIN:
+            for f in FBIN:
                 def msm(f=f):
                     self.fn2(f, T, L, Gt)
                     self.modi_add(T)
@@ -506,11 +562,11 @@ class Gen:
 
                 self.body(f"MSMB{f}", msm)
                 self.body(f"SMMB{f}", smm)
-                self.case(fx("MS_M", f, 0), lambda: self.mem_pop(L), then=f"MSMB{f}")
-                self.case(fx("SM_M", f, 0), lambda: self.mem_pop(L), then=f"SMMB{f}")
+                self.case(fx("MS_M", bi(f), 0), lambda: self.mem_pop(L), then=f"MSMB{f}")
+                self.case(fx("SM_M", bi(f), 0), lambda: self.mem_pop(L), then=f"SMMB{f}")
                 for q in range(NSM):
-                    self.case(fx("MSS_M", f * NSM + q, 0), lambda q=q: sm_pop(q), then=f"MSMB{f}")
-                    self.case(fx("SMS_M", f * NSM + q, 0), lambda q=q: sm_pop(q), then=f"SMMB{f}")
+                    self.case(fx("MSS_M", bi(f) * NSM + q, 0), lambda q=q: sm_pop(q), then=f"MSMB{f}")
+                    self.case(fx("SMS_M", bi(f) * NSM + q, 0), lambda q=q: sm_pop(q), then=f"SMMB{f}")
 
         # the cases in code order (see layout_key)
         for _, chunk in sorted(self.chunks, key=lambda c: c[0]):
@@ -570,7 +626,8 @@ def render_isa() -> str:
         "// MAXS local-memory entries per thread).  A level form's",
         "// opcode is base + sub * NREG + d, a memory form's base + sub; sub is the",
         "// unary index f - F_SIN, the binary function f, or for the forms that exist",
-        "// only for non-commutative functions nc_index(f).  Word: .x = opcode |",
+        "// only for non-commutative functions nc_index(f), bin_index(f) for the",
+        "// others.  Word: .x = opcode |",
         "// out_index << 16 (Modi forms), .y = operand; VC/CV/CC take a second word",
         "// whose .x is the feature index (VC, CV) or the bits of the second constant",
         "// (CC).",
@@ -590,8 +647,11 @@ def render_isa() -> str:
         out.append(f"  {name} = {FX_BASE[name]},")
     out.append(f"  COUNT = {FX_COUNT}")
     out.append("};")
-    out.append("// index of a non-commutative binary function among the two-entry forms")
-    out.append("__host__ __device__ constexpr int nc_index(int f) { return f == 1 ? 0 : f == 3 ? 1 : -1; }")
+    out.append("// index of a non-commutative binary form's function among the RV/RC/CV/RS/SM forms")
+    out.append("__host__ __device__ constexpr int nc_index(int f) { return f == 1 ? 0 : f == 3 ? 1 : f == 10 ? 2 : -1; }")
+    out.append("// index of a binary form's function (ite's branch selection after the binary functions)")
+    out.append("__host__ __device__ constexpr int bin_index(int f) { return f <= 4 ? f : f == 10 ? 5 : -1; }")
+    out.append(f"constexpr int MAXC = {MAXC};   // pending ite conditions the 64-bit condition stack holds")
     out.append("}  // namespace fx")
     out.append("}  // namespace tgp")
     return "\n".join(out) + "\n"

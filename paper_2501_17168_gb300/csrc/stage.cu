@@ -19,7 +19,8 @@ namespace tgp {
 // per-warp shared memory: node records of one tree, lmax entries per array
 // (lmax = the longest max_len of the launch, a multiple of 16)
 struct NodeSmem {
-  uint32_t* info;   // bits 0-3 func, 4-5 kind (0 var,1 const,2 unary,3 binary), 6 modi, 8-15 out
+  uint32_t* info;   // bits 0-3 func, 4-6 kind (0 var, 1 const, 2 unary, 3 binary, 4 ternary),
+                    // 7 modi, 8-15 out, 16 scratch of the compiler
   uint32_t* leaf;   // variable index or constant bits
   int16_t* sz;      // subtree size (0 = not a valid size)
   int16_t* par;     // parent index
@@ -44,7 +45,7 @@ constexpr int STAGE_WARPS = 4;
 
 __device__ __forceinline__ bool is_int(float v) { return isfinite(v) && v == floorf(v); }
 
-__device__ __forceinline__ int kind_of(uint32_t in) { return (in >> 4) & 3; }
+__device__ __forceinline__ int kind_of(uint32_t in) { return (in >> 4) & 7; }
 
 // Emits the forward program of a validated tree in the level-register
 // instruction set (isa_fwd.cuh): the value of a subtree evaluated at level d
@@ -56,9 +57,22 @@ __device__ __forceinline__ int kind_of(uint32_t in) { return (in >> 4) & 3; }
 // program would exceed cap words or the memory stack (neither happens for
 // trees of up to 1024 nodes: every non-leaf subtree has a leaf without a
 // word of its own, and the Sethi-Ullman number stays below NREG + MAXS).
+// bit of a ternary node's info word once its condition has been pushed
+constexpr uint32_t COND_DONE = 1u << 16;
+
+// The two operands of node q's binary instruction: a binary node's children,
+// or the branches (second and third children) of an ite node, whose first
+// child is its condition.
+__device__ __forceinline__ void bin_ops(const NodeSmem& ns, int q, int* ca, int* cb) {
+  int a = q + 1;
+  if (kind_of(ns.info[q]) == 4) a += ns.sz[a];
+  *ca = a;
+  *cb = a + ns.sz[a];
+}
+
 __device__ int compile_fx(NodeSmem& ns, bool single_out, uint2* prog, int cap) {
   using namespace fx;
-  int pc = 0, n = 0, sdepth = 0;
+  int pc = 0, n = 0, sdepth = 0, cdepth = 0;
   bool down = true;
   auto put = [&](uint32_t x, uint32_t y) {
     if (pc >= cap) return false;
@@ -76,7 +90,7 @@ __device__ int compile_fx(NodeSmem& ns, bool single_out, uint2* prog, int cap) {
         down = false;
         continue;
       }
-      const bool modi = in & 64;
+      const bool modi = in & 128;
       const int f = in & 15;
       const uint32_t o16 = modi ? ((in >> 8) & 255) << 16 : 0;
       if (k == 2) {
@@ -91,18 +105,35 @@ __device__ int compile_fx(NodeSmem& ns, bool single_out, uint2* prog, int cap) {
         n = c;
         continue;
       }
-      const int ca = n + 1, cb = ca + ns.sz[ca];
+      if (k == 4 && !(in & COND_DONE)) {
+        // ite: the condition first, at the node's level; its sign bits go to
+        // the condition stack and the branches follow as a binary form
+        const int a = n + 1, ka = kind_of(ns.info[a]);
+        if (ka <= 1) {
+          if (cdepth >= MAXC || !put((ka == 0 ? CDV : CDC) + lv, ns.leaf[a])) return -1;
+          ++cdepth;
+          ns.info[n] = in | COND_DONE;
+          continue;
+        }
+        ns.slot[a] = lv;
+        n = a;
+        continue;
+      }
+      const int fb = k == 4 ? (int)F_ITE : f, bfn = bin_index(fb);
+      int ca, cb;
+      bin_ops(ns, n, &ca, &cb);
       const int ka = kind_of(ns.info[ca]), kb = kind_of(ns.info[cb]);
       if (ka <= 1 && kb <= 1 && !modi) {  // two leaves: one instruction
         const uint32_t la = ns.leaf[ca], lb = ns.leaf[cb];
-        const int nc = nc_index(f);
+        const int nc = nc_index(fb);
         bool ok;
-        if (ka == 0 && kb == 0) ok = put(VV + f * NREG + lv, la | (lb << 16));
-        else if (ka == 0) ok = put(VC + f * NREG + lv, lb) && put(la, 0);
-        else if (kb == 0 && nc < 0) ok = put(VC + f * NREG + lv, la) && put(lb, 0);
+        if (ka == 0 && kb == 0) ok = put(VV + bfn * NREG + lv, la | (lb << 16));
+        else if (ka == 0) ok = put(VC + bfn * NREG + lv, lb) && put(la, 0);
+        else if (kb == 0 && nc < 0) ok = put(VC + bfn * NREG + lv, la) && put(lb, 0);
         else if (kb == 0) ok = put(CV + nc * NREG + lv, la) && put(lb, 0);
-        else ok = put(CC + f * NREG + lv, la) && put(lb, 0);
+        else ok = put(CC + bfn * NREG + lv, la) && put(lb, 0);
         if (!ok) return -1;
+        if (k == 4) --cdepth;  // the selection pops the condition
         down = false;
         continue;
       }
@@ -116,21 +147,31 @@ __device__ int compile_fx(NodeSmem& ns, bool single_out, uint2* prog, int cap) {
     const int q = ns.par[n];
     const uint32_t qin = ns.info[q];
     const int qk = kind_of(qin), f = qin & 15, lv = ns.slot[q];
-    const bool modi = qin & 64;
+    const bool modi = qin & 128;
     const uint32_t o16 = modi ? ((qin >> 8) & 255) << 16 : 0;
+    if (qk == 4 && n == q + 1) {  // ite's condition is done: push its sign bits
+      if (cdepth >= MAXC || !put(CD + lv, 0)) return -1;
+      ++cdepth;
+      ns.info[q] = qin | COND_DONE;
+      n = q;
+      down = true;
+      continue;
+    }
     uint32_t x, y = 0;
     if (qk == 2) {
       x = (modi ? UN_M : UN) + (f - F_SIN) * NREG + lv;
     } else {
-      const int ca = q + 1, cb = ca + ns.sz[ca];
+      const int fb = qk == 4 ? (int)F_ITE : f, bfn = bin_index(fb);
+      int ca, cb;
+      bin_ops(ns, q, &ca, &cb);
       const int ka = kind_of(ns.info[ca]), kb = kind_of(ns.info[cb]);
-      const int nc = nc_index(f);
+      const int nc = nc_index(fb);
       if (kb <= 1) {  // b is a leaf, a is in G[lv]
-        x = (modi ? (kb == 0 ? BV_M : BC_M) : (kb == 0 ? BV : BC)) + f * NREG + lv;
+        x = (modi ? (kb == 0 ? BV_M : BC_M) : (kb == 0 ? BV : BC)) + bfn * NREG + lv;
         y = ns.leaf[cb];
       } else if (ka <= 1) {  // a is a leaf, b is in G[lv]
-        if (modi) x = (ka == 0 ? RV_M : RC_M) + f * NREG + lv;
-        else if (nc < 0) x = (ka == 0 ? BV : BC) + f * NREG + lv;
+        if (modi) x = (ka == 0 ? RV_M : RC_M) + bfn * NREG + lv;
+        else if (nc < 0) x = (ka == 0 ? BV : BC) + bfn * NREG + lv;
         else x = (ka == 0 ? RV : RC) + nc * NREG + lv;
         y = ns.leaf[ca];
       } else {
@@ -150,28 +191,29 @@ __device__ int compile_fx(NodeSmem& ns, bool single_out, uint2* prog, int cap) {
           continue;
         }
         if (!mem) {  // first operand in G[lv], second in G[lv+1]
-          if (a_first) x = (modi ? BS_M : BS) + f * NREG + lv;
-          else if (modi) x = RS_M + f * NREG + lv;
-          else if (nc < 0) x = BS + f * NREG + lv;
+          if (a_first) x = (modi ? BS_M : BS) + bfn * NREG + lv;
+          else if (modi) x = RS_M + bfn * NREG + lv;
+          else if (nc < 0) x = BS + bfn * NREG + lv;
           else x = RS + nc * NREG + lv;
         } else {  // first operand on the memory stack, second in G[NREG-1]
           const int sq = --sdepth;
           if (sq < NSM) {  // entry in the warp's shared-memory rows
-            if (a_first) x = (modi ? MSS_M : MSS) + f * NSM + sq;
-            else if (modi) x = SMS_M + f * NSM + sq;
-            else if (nc < 0) x = MSS + f * NSM + sq;
+            if (a_first) x = (modi ? MSS_M : MSS) + bfn * NSM + sq;
+            else if (modi) x = SMS_M + bfn * NSM + sq;
+            else if (nc < 0) x = MSS + bfn * NSM + sq;
             else x = SMS + nc * NSM + sq;
           } else if (a_first) {
-            x = (modi ? MS_M : MS) + f;
+            x = (modi ? MS_M : MS) + bfn;
           } else if (modi) {
-            x = SM_M + f;
+            x = SM_M + bfn;
           } else if (nc < 0) {
-            x = MS + f;
+            x = MS + bfn;
           } else {
             x = SM + nc;
           }
         }
       }
+      if (qk == 4) --cdepth;  // the selection pops the condition
     }
     if (!put(x | o16, y)) return -1;
     n = q;
@@ -247,7 +289,7 @@ __device__ int compile_adj(NodeSmem& ns, bool single_out, uint2* prog) {
     }
     // ---- emit the instruction of node q
     int f = qin & 15;
-    bool modi = qin & 64;
+    bool modi = qin & 128;
     uint32_t o8 = ((qin >> 8) & 255) << 8;
     uint2 ins;
     ins.y = 0;
@@ -321,7 +363,8 @@ __global__ void __launch_bounds__(STAGE_WARPS * 32) stage_kernel(const __grid_co
         uint32_t info = 0, leaf = 0;
         int base = ty >= 0 ? (ty & ~T_MODI) : -1;
         bool modi = ty >= 0 && (ty & T_MODI);
-        if (!(ty == 0 || ty == 1 || ty == 2 || ty == 3 || ty == 18 || ty == 19)) {
+        if (!(ty == 0 || ty == 1 || ty == 2 || ty == 3 || ty == 4 || ty == 18 || ty == 19 ||
+              ty == 20)) {
           st |= S_TYPE;
         } else if (base == T_VAR) {
           if (!is_int(vv) || vv < 0.0f || vv >= (float)a.n_features) st |= S_VAR;
@@ -337,13 +380,14 @@ __global__ void __launch_bounds__(STAGE_WARPS * 32) stage_kernel(const __grid_co
           } else {
             int iv = (int)vv;
             int f = iv & 255, o = iv >> 8;
-            if (f >= F_COUNT || arity(f) != (base == T_UFUNC ? 1 : 2)) st |= S_FUNC;
+            // the type names the arity: 2 unary, 3 binary, 4 ternary
+            if (f >= F_COUNT || arity(f) != base - 1) st |= S_FUNC;
             if (modi) {
               if (o >= a.n_outputs) st |= S_MODI;
             } else if (o != 0) {
               st |= S_FUNC;
             }
-            info = (uint32_t)(f & 15) | ((base == T_UFUNC ? 2u : 3u) << 4) | (modi ? 64u : 0u) |
+            info = (uint32_t)(f & 15) | ((uint32_t)base << 4) | (modi ? 128u : 0u) |
                    ((uint32_t)(o & 255) << 8);
             modi_here |= modi;
           }
@@ -367,7 +411,7 @@ __global__ void __launch_bounds__(STAGE_WARPS * 32) stage_kernel(const __grid_co
           } else if (k == 2) {
             if (s < 2 || ns.sz[i + 1] == 0 || s != 1 + ns.sz[i + 1]) bad = 1;
             else ns.par[i + 1] = (int16_t)i;
-          } else {
+          } else if (k == 3) {
             if (s < 3) { bad = 1; continue; }
             int s1 = ns.sz[i + 1];
             int c2 = i + 1 + s1;
@@ -376,6 +420,19 @@ __global__ void __launch_bounds__(STAGE_WARPS * 32) stage_kernel(const __grid_co
             if (s2 == 0 || s != 1 + s1 + s2) { bad = 1; continue; }
             ns.par[i + 1] = (int16_t)i;
             ns.par[c2] = (int16_t)i;
+          } else {  // ternary: three children tile [i+1, i+s)
+            if (s < 4) { bad = 1; continue; }
+            int s1 = ns.sz[i + 1];
+            int c2 = i + 1 + s1;
+            if (s1 == 0 || c2 >= i + s) { bad = 1; continue; }
+            int s2 = ns.sz[c2];
+            int c3 = c2 + s2;
+            if (s2 == 0 || c3 >= i + s) { bad = 1; continue; }
+            int s3 = ns.sz[c3];
+            if (s3 == 0 || s != 1 + s1 + s2 + s3) { bad = 1; continue; }
+            ns.par[i + 1] = (int16_t)i;
+            ns.par[c2] = (int16_t)i;
+            ns.par[c3] = (int16_t)i;
           }
         }
         if (__any_sync(0xffffffffu, bad)) st |= S_SIZE;
@@ -394,7 +451,10 @@ __global__ void __launch_bounds__(STAGE_WARPS * 32) stage_kernel(const __grid_co
         } else if (k == 2) {
           nd = ns.need[i + 1];
         } else {
-          int ca = i + 1, cb = ca + ns.sz[ca];
+          // a binary node's operands, or an ite node's branches (its
+          // condition is evaluated first at the same level, then popped)
+          int ca, cb;
+          bin_ops(ns, i, &ca, &cb);
           bool la = kind_of(ns.info[ca]) <= 1, lb = kind_of(ns.info[cb]) <= 1;
           if (lb) nd = ns.need[ca];
           else if (la) nd = ns.need[cb];
@@ -402,17 +462,22 @@ __global__ void __launch_bounds__(STAGE_WARPS * 32) stage_kernel(const __grid_co
             int na = ns.need[ca], nb = ns.need[cb];
             nd = na >= nb ? max(na, nb + 1) : max(nb, na + 1);
           }
+          if (k == 4) nd = max(nd, (int)ns.need[i + 1]);
         }
         ns.need[i] = (uint8_t)min(nd, 255);
       }
       uint2* prog = a.prog + p * a.pcap;
+      bool ternary = false;
+      for (int i = 0; i < len; ++i) ternary |= kind_of(ns.info[i]) == 4;
       if (!a.want_nodes) {
         pc = compile_fx(ns, a.n_outputs == 1 && !modi_here, prog, a.pcap);
+      } else if (ternary) {
+        pc = -2;  // the adjoint set has no ite
       } else {
         pc = compile_adj(ns, a.n_outputs == 1 && !modi_here, prog);
       }
       if (pc < 0) {
-        st = S_DEPTH;
+        st = pc == -2 ? S_NOADJ : S_DEPTH;
         pc = 0;
       }
     }

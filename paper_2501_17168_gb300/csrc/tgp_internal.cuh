@@ -33,10 +33,11 @@
 namespace tgp {
 
 // ------------------------------------------------------------- encoding
-enum NodeType : int { T_VAR = 0, T_CONST = 1, T_UFUNC = 2, T_BFUNC = 3, T_MODI = 16 };
-enum Func : int { F_ADD = 0, F_SUB, F_MUL, F_PDIV, F_MAX, F_SIN, F_COS, F_PLOG, F_CEXP, F_TAN, F_COUNT };
+enum NodeType : int { T_VAR = 0, T_CONST = 1, T_UFUNC = 2, T_BFUNC = 3, T_TFUNC = 4, T_MODI = 16 };
+enum Func : int { F_ADD = 0, F_SUB, F_MUL, F_PDIV, F_MAX, F_SIN, F_COS, F_PLOG, F_CEXP, F_TAN, F_ITE, F_COUNT };
 enum TreeStatus : int {
-  S_LEN = 1, S_TYPE = 2, S_FUNC = 4, S_VAR = 8, S_MODI = 16, S_CONST = 32, S_SIZE = 64, S_DEPTH = 128
+  S_LEN = 1, S_TYPE = 2, S_FUNC = 4, S_VAR = 8, S_MODI = 16, S_CONST = 32, S_SIZE = 64, S_DEPTH = 128,
+  S_NOADJ = 256   // a node the adjoint does not differentiate (ite)
 };
 
 constexpr int R = 8;            // register slots below the accumulator
@@ -75,7 +76,7 @@ enum Op : uint32_t {
   OP_COUNT = 235
 };
 
-__host__ __device__ constexpr int arity(int f) { return f <= F_MAX ? 2 : 1; }
+__host__ __device__ constexpr int arity(int f) { return f <= F_MAX ? 2 : f == F_ITE ? 3 : 1; }
 
 // ------------------------------------------------------------- FP32 functions
 // The function bodies (protected division and log with the 1e-6f guard,

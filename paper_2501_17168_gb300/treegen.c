@@ -12,7 +12,10 @@
  * has no unary function, n is odd.  A node with n = 1 is a leaf; otherwise a
  * function id is drawn uniformly from the set, and if its arity cannot
  * produce n nodes under the cap the other arity is used.  A binary node splits
- * its n-1 descendants uniformly over the feasible (left, right) pairs.
+ * its n-1 descendants uniformly over the feasible (left, right) pairs; a
+ * ternary node (id 10) draws its first and second child sizes uniformly over
+ * their feasible ranges in turn (function sets with a ternary id also hold a
+ * unary one, so every size fits).
  * Leaves: the number of constants is Binomial(n_leaves, 1 - p_var) capped at
  * max_consts, placed on uniformly chosen leaves; the rest are variables with
  * a uniform feature index.  Constants are uniform on [c_lo, c_hi).
@@ -54,12 +57,12 @@ typedef struct {
   int nthreads;
 } gen_t;
 
-enum { T_VAR = 0, T_CONST = 1, T_UFUNC = 2, T_BFUNC = 3, T_MODI = 16 };
+enum { T_VAR = 0, T_CONST = 1, T_UFUNC = 2, T_BFUNC = 3, T_TFUNC = 4, T_MODI = 16 };
 
-static int arity(int f) { return f <= 4 ? 2 : 1; }
+static int arity(int f) { return f <= 4 ? 2 : f == 10 ? 3 : 1; }
 
 typedef struct {
-  int* kind;   /* 0 leaf, 1 unary, 2 binary */
+  int* kind;   /* 0 leaf, 1 unary, 2 binary, 3 ternary */
   int* func;
   int* size;
   int n;
@@ -99,6 +102,24 @@ static void grow(const gen_t* g, sm64_t* r, int n0, shape_t* s, int has_u, int h
         b_ok = a_lo <= a_hi;
       }
     }
+    if (ar == 3) {
+      /* three children of at most M nodes each, only with a unary id in the
+       * set (no parity constraint on the sizes) */
+      long lo1 = n - 1 - 2 * M, hi1 = M < n - 3 ? M : n - 3;
+      if (lo1 < 1) lo1 = 1;
+      if (has_u && n >= 4 && lo1 <= hi1) {
+        int a = sm64_int(r, (int)lo1, (int)hi1);
+        long lo2 = n - 1 - a - M, hi2 = M < n - 2 - a ? M : n - 2 - a;
+        if (lo2 < 1) lo2 = 1;
+        int b = sm64_int(r, (int)lo2, (int)hi2);
+        s->kind[i] = 3; s->func[i] = f;
+        stk_n[sp] = n - 1 - a - b; stk_d[sp] = d - 1; sp++;
+        stk_n[sp] = b; stk_d[sp] = d - 1; sp++;
+        stk_n[sp] = a; stk_d[sp] = d - 1; sp++;
+        continue;
+      }
+      ar = b_ok ? 2 : 1;
+    }
     if (ar == 1 && !u_ok) ar = 2;
     if (ar == 2 && !b_ok) ar = 1;
     if (ar == 1) {
@@ -128,7 +149,7 @@ static void grow(const gen_t* g, sm64_t* r, int n0, shape_t* s, int has_u, int h
 static void gen_tree(const gen_t* g, long p) {
   sm64_t r = {g->seed * 0xD1B54A32D192ED03ULL + (uint64_t)p * 0x9E3779B97F4A7C15ULL + 1};
   int has_u = 0, has_b = 0;
-  for (int k = 0; k < g->n_fset; ++k) { if (arity(g->fset[k]) == 1) has_u = 1; else has_b = 1; }
+  for (int k = 0; k < g->n_fset; ++k) { if (arity(g->fset[k]) == 1) has_u = 1; else if (arity(g->fset[k]) == 2) has_b = 1; }
   int cap = g->len_hi;
   shape_t s;
   s.kind = (int*)malloc(sizeof(int) * cap * 3);
@@ -164,7 +185,7 @@ static void gen_tree(const gen_t* g, long p) {
   for (int i = 0; i < n; ++i) {
     sz[i] = (float)s.size[i];
     if (s.kind[i] == 0) { ty[i] = T_VAR; va[i] = (float)sm64_int(&r, 0, g->n_features - 1); }
-    else { ty[i] = s.kind[i] == 1 ? T_UFUNC : T_BFUNC; va[i] = (float)s.func[i]; }
+    else { ty[i] = s.kind[i] == 1 ? T_UFUNC : s.kind[i] == 2 ? T_BFUNC : T_TFUNC; va[i] = (float)s.func[i]; }
   }
   for (int k = 0; k < n_const; ++k) {
     int i = leaves[k];

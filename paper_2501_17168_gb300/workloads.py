@@ -9,12 +9,12 @@ the tests, the library itself in the benchmark), so that no arithmetic of the
 method lives in this module.
 
 Encoding (our reading; Sec. III-A leaves the codes open):
-  type  0 variable, 1 constant, 2 unary function, 3 binary function;
-        +16 marks a Modi node (Sec. IV-C).
+  type  0 variable, 1 constant, 2 unary function, 3 binary function,
+        4 ternary function; +16 marks a Modi node (Sec. IV-C).
   value variable -> feature index, constant -> the constant,
         function -> func_id + 256 * output_index (output index on Modi only).
   func  0 add, 1 sub, 2 mul, 3 protected div, 4 max, 5 sin, 6 cos,
-        7 protected log, 8 clamped exp, 9 tan.
+        7 protected log, 8 clamped exp, 9 tan, 10 ite (a > 0 ? b : c).
 """
 from __future__ import annotations
 
@@ -27,15 +27,17 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-VAR, CONST, UFUNC, BFUNC, MODI = 0, 1, 2, 3, 16
-ADD, SUB, MUL, PDIV, MAX, SIN, COS, PLOG, CEXP, TAN = range(10)
-FUNC_NAMES = ("add", "sub", "mul", "pdiv", "max", "sin", "cos", "plog", "cexp", "tan")
-ARITY = (2, 2, 2, 2, 2, 1, 1, 1, 1, 1)
+VAR, CONST, UFUNC, BFUNC, TFUNC, MODI = 0, 1, 2, 3, 4, 16
+ADD, SUB, MUL, PDIV, MAX, SIN, COS, PLOG, CEXP, TAN, ITE = range(11)
+FUNC_NAMES = ("add", "sub", "mul", "pdiv", "max", "sin", "cos", "plog", "cexp", "tan", "ite")
+ARITY = (2, 2, 2, 2, 2, 1, 1, 1, 1, 1, 3)
 
 #: function set of the plain-SR workloads
 SR_FSET = (ADD, SUB, MUL, PDIV, SIN, COS, PLOG, CEXP, MAX)
 #: function set of the paper's experiments (Table "Configuration of GP")
 PAPER_FSET = (ADD, SUB, MUL, PDIV, SIN, COS, TAN)
+#: function set with the ternary if-then-else (classification-style rules)
+TERNARY_FSET = SR_FSET + (ITE,)
 #: ground-truth trees use a tame subset so that targets stay finite
 GT_FSET = (ADD, SUB, MUL, SIN, COS, MAX)
 
@@ -143,7 +145,7 @@ def encode(tokens, ld: int | None = None) -> Population:
         else:
             name, out = (tok, None) if isinstance(tok, str) else tok
             f = FUNC_NAMES.index(name)
-            t[i] = (UFUNC if ARITY[f] == 1 else BFUNC) | (MODI if out is not None else 0)
+            t[i] = (UFUNC, BFUNC, TFUNC)[ARITY[f] - 1] | (MODI if out is not None else 0)
             v[i] = f + 256 * (out or 0)
             ar.append(ARITY[f])
 

@@ -97,8 +97,10 @@ MSE_STRICT_MARGIN = 0.15    # per-tree MSEs
 GRAD_STRICT_MARGIN = 0.12   # gradient elements
 
 
-def _apply32(f, a, b=None):
+def _apply32(f, a, b=None, c=None):
     with np.errstate(all="ignore"):
+        if f == 10:
+            return np.where(a > F32(0), b, c).astype(F32)
         if f == 0:
             return a + b
         if f == 1:
@@ -149,12 +151,13 @@ def f32_eval(type_, val, size, X, n_outputs=1):
                 continue
             f, o = int(v) % 256, int(v) // 256
             a = stack.pop()
-            b = stack.pop() if base == 3 else None
-            r = _apply32(f, a, b).astype(F32)
+            b = stack.pop() if base >= 3 else None
+            c = stack.pop() if base == 4 else None
+            r = _apply32(f, a, b, c).astype(F32)
             if modi:
                 any_modi = True
                 acc[o] = (acc[o] + r).astype(F32)
-                stack.append(b if b is not None else a)
+                stack.append(c if c is not None else b if b is not None else a)
             else:
                 stack.append(r)
         if n_outputs == 1 and not any_modi:
@@ -212,10 +215,12 @@ def assert_mse_strict_floor(gpu_mse, ref, allow, type_, val, size, X, y, n_outpu
 TOL_GRAD = 1e-3
 
 
-def _children(type_row, val_row, L):
-    """First and second child of every node by an arity parse of the prefix."""
+def _children(type_row, val_row, L, third=False):
+    """First, second (and third) child of every node by an arity parse of
+    the prefix."""
     c1 = np.full(L, -1, np.int64)
     c2 = np.full(L, -1, np.int64)
+    c3 = np.full(L, -1, np.int64)
     end = np.zeros(L, np.int64)
     for i in range(L - 1, -1, -1):
         base = int(type_row[i]) & ~16
@@ -223,12 +228,14 @@ def _children(type_row, val_row, L):
             end[i] = i + 1
             continue
         c1[i] = i + 1
-        if base == 3:
-            c2[i] = end[i + 1]
+        end[i] = end[i + 1]
+        if base >= 3:
+            c2[i] = end[i]
             end[i] = end[c2[i]]
-        else:
-            end[i] = end[i + 1]
-    return c1, c2
+        if base == 4:
+            c3[i] = end[i]
+            end[i] = end[c3[i]]
+    return (c1, c2, c3) if third else (c1, c2)
 
 
 ACC_TERMS = 512
@@ -255,7 +262,7 @@ def f32_grad(type_, val, size, X, y, g, n_outputs=1):
                 continue
             L = int(L)
             tr, vr = type_[k], val[k]
-            c1, c2 = _children(tr, vr, L)
+            c1, c2, c3 = _children(tr, vr, L, third=True)
             v = [None] * L
             acc = np.zeros((n_outputs, D), F32)
             any_modi = False
@@ -270,11 +277,12 @@ def f32_grad(type_, val, size, X, y, g, n_outputs=1):
                 f, o = int(vr[i]) % 256, int(vr[i]) // 256
                 a = v[c1[i]]
                 b = v[c2[i]] if c2[i] >= 0 else None
-                r = _apply32(f, a, b).astype(F32)
+                cc = v[c3[i]] if c3[i] >= 0 else None
+                r = _apply32(f, a, b, cc).astype(F32)
                 if modi:
                     any_modi = True
                     acc[o] = (acc[o] + r).astype(F32)
-                    v[i] = b if b is not None else a
+                    v[i] = cc if cc is not None else b if b is not None else a
                 else:
                     v[i] = r
             out = acc.copy()
@@ -301,6 +309,17 @@ def f32_grad(type_, val, size, X, y, g, n_outputs=1):
                 af = seed[o] if modi else adj[i]
                 one, zero = F32(1), F32(0)
                 da = db = None
+                if f == 10:
+                    # the adjoint goes to the chosen branch, the condition gets none
+                    pos = a > F32(0)
+                    adj[c1[i]] = np.zeros(D, F32)
+                    gb = np.where(pos, af, zero).astype(F32)
+                    gc = np.where(pos, zero, af).astype(F32)
+                    if modi:
+                        gc = (gc + adj[i]).astype(F32)
+                    adj[c2[i]] = gb
+                    adj[c3[i]] = gc
+                    continue
                 if f == 0:
                     da, db = np.ones(D, F32), np.ones(D, F32)
                 elif f == 1:

@@ -654,3 +654,84 @@ def test_gradient_bound_is_tight_on_well_conditioned_trees(orc):
     _, _, _, _, egv, _ = orc.grad(p.type, p.val, p.size, Xg, np.zeros((1, 1), np.float32), 1.0,
                                   with_err=True)
     assert not np.isfinite(err[0, 0, 0]) and np.isinf(egv[0, 1])
+
+
+# ---------------------------------------------------------- ternary ite
+def test_ite_selects_by_the_sign_of_its_condition(orc):
+    """ite(a, b, c) = a > 0 ? b : c (the library's ternary function; type
+    code 4, the arity the encoding's (type, value) pair names, Sec. III-A):
+    exact selection, a zero, negative zero or NaN condition selects c."""
+    p = _enc(["ite", ["x", 0], ["x", 1], ["x", 2]])
+    assert list(p.type[0]) == [W.TFUNC, W.VAR, W.VAR, W.VAR] and p.size[0, 0] == 4
+    conds = np.array([1.0, -1.0, 0.0, -0.0, np.nan, 1e-45, -1e-45, np.inf, -np.inf, 3e38],
+                     np.float32)
+    rng = np.random.default_rng(21)
+    X = np.stack([conds, rng.standard_normal(10), rng.standard_normal(10)], 1).astype(np.float32)
+    out, st = orc.evaluate(p.type, p.val, p.size, X)
+    assert st[0] == 0
+    want = np.where(X[:, 0] > 0, X[:, 1], X[:, 2]).astype(np.float64)
+    np.testing.assert_array_equal(out[0, 0], want)
+
+
+def test_ite_modi_passes_its_third_child(orc):
+    # add·M(o0)(ite·M(o1)(x0, x1, x2), x3): output 1 = ite(x0, x1, x2); the
+    # ite node hands its parent x2, so output 0 = x2 + x3
+    p = _enc([("add", 0), ("ite", 1), ["x", 0], ["x", 1], ["x", 2], ["x", 3]])
+    X = np.random.default_rng(22).standard_normal((64, 4)).astype(np.float32)
+    out, st = orc.evaluate(p.type, p.val, p.size, X, n_outputs=2)
+    x = X.astype(np.float64)
+    np.testing.assert_array_equal(out[0, 1], np.where(x[:, 0] > 0, x[:, 1], x[:, 2]))
+    np.testing.assert_allclose(out[0, 0], x[:, 2] + x[:, 3], rtol=1e-15)
+
+
+def test_ite_validator_and_gradient_routing(orc):
+    ok = _enc(["ite", ["x", 0], ["c", 1.0], ["x", 1]])
+    t, v, s = ok.type.copy(), ok.val.copy(), ok.size.copy()
+    st, _ = orc.validate(t, v, s, 2)
+    assert st[0] == 0
+    bad = t.copy(); bad[0, 0] = W.BFUNC          # ite under the binary type
+    assert orc.validate(bad, v, s, 2)[0][0] & orc.ST_FUNC
+    bad = t.copy(); bv = v.copy(); bv[0, 0] = W.ADD   # a binary id under the ternary type
+    assert orc.validate(bad, bv, s, 2)[0][0] & orc.ST_FUNC
+    bs = s.copy(); bs[0, 0] = 3                    # sizes that do not tile three children
+    assert orc.validate(t, v, bs, 2)[0][0] & orc.ST_SIZE
+    # d MSE / d x1 reaches x1 only where x0 <= 0; the condition gets nothing
+    p = _enc(["mul", ["c", 1.5], "ite", ["x", 0], ["x", 1], ["x", 2]])
+    X = np.random.default_rng(23).standard_normal((200, 3)).astype(np.float32)
+    y = np.zeros((200, 1), np.float32)
+    m, gv, gx, st = orc.grad(p.type, p.val, p.size, X, y, 1.0)
+    x = X.astype(np.float64)
+    sel = np.where(x[:, 0] > 0, x[:, 1], x[:, 2])
+    o = 1.5 * sel
+    np.testing.assert_allclose(gx[:, 0], 0.0)
+    np.testing.assert_allclose(gx[:, 1], np.where(x[:, 0] > 0, 2 * o * 1.5 / 200, 0.0), rtol=1e-12)
+    np.testing.assert_allclose(gx[:, 2], np.where(x[:, 0] > 0, 0.0, 2 * o * 1.5 / 200), rtol=1e-12)
+    np.testing.assert_allclose(gv[0, 1], np.sum(2 * o * sel / 200), rtol=1e-12)
+
+
+def test_ite_bound_is_infinite_where_the_sign_is_undecided(orc):
+    # sub(x0, x1) = 1e-30 - 1e-30 rounds exactly (0); (x0 * x1) - x2 carries
+    # rounding error around 0: the branch is undecided there
+    p = _enc(["ite", "sub", "mul", ["x", 0], ["x", 1], ["x", 2], ["c", 1.0], ["c", -1.0]])
+    X = np.array([[3.0, 1.0 / 3.0, 1.0], [3.0, 1.0, 1.0], [2.0, 2.0, 1.0]], np.float32)
+    out, err, _ = orc.evaluate(p.type, p.val, p.size, X, with_err=True)
+    assert np.isinf(err[0, 0, 0])          # 3 * fl(1/3) - 1 is within its rounding of 0
+    assert err[0, 0, 2] == 0.0 and out[0, 0, 2] == 1.0
+
+
+def test_error_bound_covers_float32_evaluation_with_ite(orc):
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from parity import f32_eval
+    pop = W.random_population(33, 300, 63, (1, 63), max_depth=8, n_features=3, fset=W.TERNARY_FSET)
+    m = W.random_population(34, 100, 63, (5, 63), max_depth=8, n_features=3, fset=W.TERNARY_FSET,
+                            n_outputs=3, modi=True)
+    assert (pop.type == W.TFUNC).sum() > 100 and (m.type == W.TFUNC + W.MODI).sum() > 5
+    X = np.random.default_rng(12).standard_normal((200, 3)).astype(np.float32)
+    for p, O in ((pop, 1), (m, 3)):
+        out, err, st = orc.evaluate(p.type, p.val, p.size, X, n_outputs=O, with_err=True)
+        assert (st == 0).all()
+        v32 = f32_eval(p.type, p.val, p.size, X, O).astype(np.float64)
+        ok = np.isfinite(err) & np.isfinite(out)
+        assert ok.mean() > 0.8
+        assert not (np.abs(v32[ok] - out[ok]) > err[ok]).any()
