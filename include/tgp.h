@@ -276,6 +276,16 @@ tgp_status tgp_eval_backward(const tgp_population* pop, const tgp_data* data, co
                              float* grad_value, float* grad_X, int32_t* tree_status, void* ws,
                              size_t ws_bytes, void* stream);
 
+/* tgp_eval_backward with call options: cfg->points_per_tile (a multiple of
+ * 128 up to 4096, 0 = the library's choice) is the point tile one CTA owns
+ * for every tree, cfg->eval_begin_event / eval_end_event bracket the adjoint
+ * kernel(s); the other fields are ignored.  TGP_ERR_UNSUPPORTED when the
+ * given tile does not fit shared memory. */
+tgp_status tgp_eval_backward_cfg(const tgp_population* pop, const tgp_data* data, const float* y,
+                                 int32_t n_outputs, const double* grad_mse, double* mse_out,
+                                 float* grad_value, float* grad_X, int32_t* tree_status, void* ws,
+                                 size_t ws_bytes, void* stream, const tgp_config* cfg);
+
 /* ---------------------------------------------------------------------------
  * Genetic operators on the same encoding (Sec. III-B "Tensorized Operations";
  * Algorithm 1).  Random choices are made by the caller: every random number

@@ -84,6 +84,11 @@ _SIGS = {
                                          ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "tgp_eval_backward_cfg": (ctypes.c_int, [_P(tgp_population), _P(tgp_data), ctypes.c_void_p,
+                                             ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                             _P(tgp_config)]),
     "tgp_fitness_mse_noalloc": (ctypes.c_int, [_P(tgp_population), _P(tgp_data), ctypes.c_void_p,
                                                ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_void_p]),

@@ -177,7 +177,7 @@ def population_to(pop, device) -> tuple:
 
 def tgp_eval_backward(type_, val, size, X, y, grad_mse, n_outputs: int = 1, max_len=None,
                       want_mse: bool = True, want_grad_value: bool = True, want_grad_X: bool = True,
-                      grad_X=None, tree_status=None):
+                      grad_X=None, tree_status=None, config=None):
     """Reverse-mode gradient of sum(grad_mse * MSE).
 
     Returns (mse [pop, O] float64 or None, grad_value [pop, ld] float32 or None,
@@ -209,9 +209,10 @@ def tgp_eval_backward(type_, val, size, X, y, grad_mse, n_outputs: int = 1, max_
         raise _lib.TGPError(_lib.TGP_ERR_INVALID_ARG, "tgp_workspace_size")
     ws = workspace(n, dev)
     ptr = lambda t: t.data_ptr() if t is not None else None
-    check(lib.tgp_eval_backward(ctypes.byref(pop), ctypes.byref(data), y.data_ptr(), n_outputs,
-                                g.data_ptr(), ptr(mse), ptr(gv), ptr(grad_X), tree_status.data_ptr(),
-                                ws.data_ptr(), ws.numel(), _stream_handle(dev)), "tgp_eval_backward")
+    check(lib.tgp_eval_backward_cfg(ctypes.byref(pop), ctypes.byref(data), y.data_ptr(), n_outputs,
+                                    g.data_ptr(), ptr(mse), ptr(gv), ptr(grad_X), tree_status.data_ptr(),
+                                    ws.data_ptr(), ws.numel(), _stream_handle(dev),
+                                    _cref(make_config(config))), "tgp_eval_backward")
     return mse, gv, grad_X, tree_status
 
 

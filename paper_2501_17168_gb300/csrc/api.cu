@@ -589,8 +589,11 @@ void cache_read(const char* path, char (*keys)[320], int n, tgp_config* out, int
 // Fused forward + reverse sweep: one CTA per point tile over all trees.
 tgp_status run_backward(const tgp_population* pop, const tgp_data* data, const float* y, int O,
                         const double* grad_mse, double* mse_out, float* grad_value, float* grad_X,
-                        int32_t* tree_status, void* ws, size_t ws_bytes, void* stream) {
+                        int32_t* tree_status, void* ws, size_t ws_bytes, void* stream,
+                        const tgp_config* cfg) {
   if (!pop_ok(pop) || !data_ok(data) || O < 1 || O > TGP_MAX_OUTPUTS) return TGP_ERR_INVALID_ARG;
+  if (cfg && (cfg->points_per_tile < 0 || cfg->points_per_tile % 128 != 0 || cfg->points_per_tile > 4096))
+    return TGP_ERR_INVALID_ARG;
   if (data->n_points < 1) return TGP_ERR_INVALID_ARG;
   if (pop->pop > 0 && (!y || !grad_mse)) return TGP_ERR_INVALID_ARG;
   DevInfo dv;
@@ -624,13 +627,14 @@ tgp_status run_backward(const tgp_population* pop, const tgp_data* data, const f
     // A tile (every tree over tp points) is a large unit of work, so prefer
     // enough tiles for several waves of the persistent grid: tiles of 512
     // points, halved while there are fewer than 4 tiles per resident CTA.
-    int tp = 512;
+    const bool fixed_tp = cfg && cfg->points_per_tile;
+    int tp = fixed_tp ? cfg->points_per_tile : 512;
     size_t smem = 0;
     int per_sm = 0;
     for (;;) {
       smem = adj_smem_bytes(K, nw, modi, w.pcap, pop->max_len, tp, data->n_features, O);
       if (smem > (size_t)dv.smem_optin) {
-        if (tp <= 32 * K) return TGP_ERR_UNSUPPORTED;
+        if (fixed_tp || tp <= 32 * K) return TGP_ERR_UNSUPPORTED;
         tp /= 2;
         continue;
       }
@@ -638,7 +642,7 @@ tgp_status run_backward(const tgp_population* pop, const tgp_data* data, const f
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nw * 32, smem) != cudaSuccess)
         return TGP_ERR_CUDA;
       if (per_sm < 1) return TGP_ERR_UNSUPPORTED;
-      if (tp <= 32 * K || cdiv(data->n_points, tp) >= 4LL * dv.sms * per_sm) break;
+      if (fixed_tp || tp <= 32 * K || cdiv(data->n_points, tp) >= 4LL * dv.sms * per_sm) break;
       tp /= 2;
     }
     AdjArgs a;
@@ -665,7 +669,13 @@ tgp_status run_backward(const tgp_population* pop, const tgp_data* data, const f
     long long grid = (long long)dv.sms * per_sm;
     if (grid > a.n_tiles) grid = a.n_tiles;
     void* args[] = {&a};
+    if (cfg && cfg->eval_begin_event &&
+        cudaEventRecord(reinterpret_cast<cudaEvent_t>(cfg->eval_begin_event), st) != cudaSuccess)
+      return TGP_ERR_CUDA;
     if (cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(nw * 32), args, smem, st) != cudaSuccess)
+      return TGP_ERR_CUDA;
+    if (cfg && cfg->eval_end_event &&
+        cudaEventRecord(reinterpret_cast<cudaEvent_t>(cfg->eval_end_event), st) != cudaSuccess)
       return TGP_ERR_CUDA;
   }
   AdjFinalArgs f;
@@ -773,7 +783,15 @@ tgp_status tgp_eval_backward(const tgp_population* pop, const tgp_data* data, co
                              float* grad_value, float* grad_X, int32_t* tree_status, void* ws,
                              size_t ws_bytes, void* stream) {
   return run_backward(pop, data, y, n_outputs, grad_mse, mse_out, grad_value, grad_X, tree_status, ws,
-                      ws_bytes, stream);
+                      ws_bytes, stream, nullptr);
+}
+
+tgp_status tgp_eval_backward_cfg(const tgp_population* pop, const tgp_data* data, const float* y,
+                                 int32_t n_outputs, const double* grad_mse, double* mse_out,
+                                 float* grad_value, float* grad_X, int32_t* tree_status, void* ws,
+                                 size_t ws_bytes, void* stream, const tgp_config* cfg) {
+  return run_backward(pop, data, y, n_outputs, grad_mse, mse_out, grad_value, grad_X, tree_status, ws,
+                      ws_bytes, stream, cfg);
 }
 
 size_t tgp_batch_workspace_size(const tgp_problem* probs, int32_t n) {
