@@ -3,14 +3,19 @@
 // of the Sec. II-A / IV-C tree semantics).
 //
 // Loss L = sum_{p,k} g[p,k] * MSE[p,k].  Work decomposition: a work item is a
-// tile of tp data points, owned by one CTA, which sweeps every tree of the
-// population over it.  Owning the tile means the gradient of X for those
-// points is accumulated in shared memory (by every warp, with shared-memory
-// reductions) and written back once with a plain read-modify-write -- no
-// global atomics on grad_X.  Warps work independently: each pulls a tree
-// (starting at a tile-dependent offset so concurrent CTAs touch different
-// trees), copies its compiled program into its own shared-memory slot, and
-// for every 32*K-point chunk of the tile
+// tile of tp data points and a range of trees (the population split into
+// tree_chunks ranges), owned by one CTA, which sweeps the range over the
+// tile.  The gradient of X for the tile's points is accumulated in shared
+// memory (by every warp, with shared-memory reductions) and written back
+// once per item: a plain read-modify-write when one item covers the whole
+// population, else global float atomics (one per point and feature per
+// item).  Large tiles amortise the per-(tree, tile) work (staging the
+// program, clearing and flushing the constant gradients); splitting the
+// population keeps enough items for the persistent grid.  Warps work
+// independently: each pulls a tree of the range (starting at a
+// tile-dependent offset so concurrent CTAs touch different trees), copies
+// its compiled program into its own shared-memory slot, and for every
+// 32*K-point chunk of the tile
 //   1. runs the program forward, writing the local partials the reverse
 //      needs to a per-thread tape in local memory (at most one entry per
 //      node, so no population x length x points activations are stored);
@@ -108,8 +113,13 @@ __global__ void __launch_bounds__(NW * 32, 3) adjoint_kernel(AdjArgs a) {
       *s_tree = 0;
     }
     __syncthreads();
-    const int tile = *s_item;
-    if (tile >= a.n_tiles) break;
+    const int item = *s_item;
+    if (item >= a.n_tiles * a.tree_chunks) break;
+    // tree-range-major: the items of one tile run at different times
+    const int tc = item / a.n_tiles, tile = item - tc * a.n_tiles;
+    const long long tr0 = (long long)tc * a.trees_per_chunk;
+    const long long tr1 = min(a.pop, tr0 + a.trees_per_chunk);
+    const long long ntr = tr1 - tr0;
     const long long p0 = (long long)tile * a.tp;
     const int np = (int)min((long long)a.tp, a.D - p0);
     // X tile (rows past the end repeat the last point so that padded lanes
@@ -131,8 +141,8 @@ __global__ void __launch_bounds__(NW * 32, 3) adjoint_kernel(AdjArgs a) {
       int t = 0;
       if (lane == 0) t = atomicAdd(s_tree, 1);
       t = __shfl_sync(0xffffffffu, t, 0);
-      if ((long long)t >= a.pop) break;
-      const long long p = (t + stagger) % a.pop;
+      if ((long long)t >= ntr) break;
+      const long long p = tr0 + (t + stagger) % ntr;
       const int plen = a.plen[p];
       if (plen <= 0) continue;
       // a tree with zero upstream gradient only needs the forward (for its
@@ -144,7 +154,7 @@ __global__ void __launch_bounds__(NW * 32, 3) adjoint_kernel(AdjArgs a) {
       // stage the program, clear the constant-gradient row, 2g/D per output
       for (int i = lane; i < plen; i += 32) prog_w[i] = a.prog[p * a.pcap + i];
       for (int i = lane; i < a.max_len; i += 32) cg_w[i] = 0.0f;
-      for (int o = lane; o < O; o += 32) g2_w[o] = (float)(2.0 * a.g[p * O + o] / (double)a.D);
+      for (int o = lane; o < O; o += 32) g2_w[o] = (float)(a.g[p * O + o] * a.two_over_D);
       __syncwarp();
       float sse[MAX_OUT];
 #pragma unroll
@@ -215,14 +225,18 @@ __global__ void __launch_bounds__(NW * 32, 3) adjoint_kernel(AdjArgs a) {
       __syncwarp();
     }
     __syncthreads();
-    // the tile's gradient of X: this CTA owns these points
+    // the tile's gradient of X over the item's trees: a plain update when
+    // this CTA owns the points, atomics when other tree ranges add to them
     if (a.grad_X) {
       for (int i = tid; i < np * a.F; i += NW * 32) {
         const int q = i / a.F, f = i - (i / a.F) * a.F;
         // tile layout [f][chunk][j][lane]: point q = chunk*CH + 128*(j/4) +
         // 4*lane + j%4
         const int c = q / CH, r = q - c * CH, h = r >> 7, rr = r & 127;
-        a.grad_X[(p0 + q) * a.F + f] += gxs[f * XS + c * CH + (4 * h + (rr & 3)) * 32 + (rr >> 2)];
+        const float v = gxs[f * XS + c * CH + (4 * h + (rr & 3)) * 32 + (rr >> 2)];
+        float* dst = a.grad_X + (p0 + q) * a.F + f;
+        if (a.tree_chunks == 1) *dst += v;
+        else if (v != 0.0f) atomicAdd(dst, v);
       }
     }
     __syncthreads();

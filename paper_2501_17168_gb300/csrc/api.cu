@@ -615,20 +615,27 @@ tgp_status run_backward(const tgp_population* pop, const tgp_data* data, const f
   tgp_status s = launch_stage(&q, 1, wsb, st, dv, true);
   if (s != TGP_OK) return s;
   const int nw = 8;
+  // the events bracket every adjoint launch of the call: begin before the
+  // first variant, end after the last (a single-output call runs both)
   for (int variant = 0; variant < 2; ++variant) {
     const bool modi = variant == 1;
     if (!modi && O > 1) continue;
+    const bool first = variant == 0 || O > 1, last = variant == 1;
     // 4 points per lane: at 8 the per-thread tape doubles and the kernel
     // runs 1.5x slower (156 vs 103 ms on the differentiation workload)
     int cap = 0;
     const int K = 4;
     const void* fn = find_adj_kernel(K, nw, modi, pop->max_len, &cap);
     if (!fn) return TGP_ERR_UNSUPPORTED;
-    // A tile (every tree over tp points) is a large unit of work, so prefer
-    // enough tiles for several waves of the persistent grid: tiles of 512
-    // points, halved while there are fewer than 4 tiles per resident CTA.
+    // Tiles of 512 points amortise the per-(tree, tile) work over 4 chunks
+    // (128 points: 127 ms, 512: 107 ms on the differentiation workload);
+    // smaller when the data has fewer points, or when wide X tiles would
+    // leave fewer than 3 CTAs per SM.  The population is then split into
+    // tree ranges so that the persistent grid gets about 8 items per CTA.
     const bool fixed_tp = cfg && cfg->points_per_tile;
     int tp = fixed_tp ? cfg->points_per_tile : 512;
+    if (!fixed_tp)
+      while (tp > 32 * K && tp / 2 >= data->n_points) tp /= 2;
     size_t smem = 0;
     int per_sm = 0;
     for (;;) {
@@ -642,9 +649,17 @@ tgp_status run_backward(const tgp_population* pop, const tgp_data* data, const f
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nw * 32, smem) != cudaSuccess)
         return TGP_ERR_CUDA;
       if (per_sm < 1) return TGP_ERR_UNSUPPORTED;
-      if (fixed_tp || tp <= 32 * K || cdiv(data->n_points, tp) >= 4LL * dv.sms * per_sm) break;
+      if (fixed_tp || tp <= 32 * K || per_sm >= 3) break;
       tp /= 2;
     }
+    const long long n_tiles = cdiv(data->n_points, tp);
+    const long long slots = (long long)dv.sms * per_sm;
+    long long chunks = cdiv(8 * slots, n_tiles);
+    const long long max_chunks = cdiv(pop->pop, 64);  // >= 64 trees (8 per warp) per item
+    if (chunks > max_chunks) chunks = max_chunks;
+    if (chunks < 1) chunks = 1;
+    const long long per_chunk = cdiv(pop->pop, chunks);
+    chunks = cdiv(pop->pop, per_chunk);
     AdjArgs a;
     a.prog = reinterpret_cast<const uint2*>(wsb + w.prog);
     a.plen = reinterpret_cast<const int*>(wsb + w.plen);
@@ -664,17 +679,20 @@ tgp_status run_backward(const tgp_population* pop, const tgp_data* data, const f
     a.mse64 = reinterpret_cast<double*>(wsb + w.mse64);
     a.grad_X = grad_X;
     a.tp = tp;
-    a.n_tiles = (int)cdiv(data->n_points, tp);
+    a.n_tiles = (int)n_tiles;
+    a.tree_chunks = (int)chunks;
+    a.trees_per_chunk = per_chunk;
+    a.two_over_D = 2.0 / (double)data->n_points;
     a.ctrl = reinterpret_cast<unsigned*>(wsb + w.ctrl);
-    long long grid = (long long)dv.sms * per_sm;
-    if (grid > a.n_tiles) grid = a.n_tiles;
+    long long grid = slots;
+    if (grid > n_tiles * chunks) grid = n_tiles * chunks;
     void* args[] = {&a};
-    if (cfg && cfg->eval_begin_event &&
+    if (first && cfg && cfg->eval_begin_event &&
         cudaEventRecord(reinterpret_cast<cudaEvent_t>(cfg->eval_begin_event), st) != cudaSuccess)
       return TGP_ERR_CUDA;
     if (cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(nw * 32), args, smem, st) != cudaSuccess)
       return TGP_ERR_CUDA;
-    if (cfg && cfg->eval_end_event &&
+    if (last && cfg && cfg->eval_end_event &&
         cudaEventRecord(reinterpret_cast<cudaEvent_t>(cfg->eval_end_event), st) != cudaSuccess)
       return TGP_ERR_CUDA;
   }

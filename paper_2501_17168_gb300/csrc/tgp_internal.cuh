@@ -176,6 +176,9 @@ struct AdjArgs {
   double* mse64;       // [pop, O] sum of squared residuals (FP64)
   float* grad_X;       // [D, F] accumulated into (may be null)
   int tp, n_tiles;
+  int tree_chunks;           // the population split into this many tree ranges
+  long long trees_per_chunk;
+  double two_over_D;         // 2 / n_points: dL/d(output) = g (o - y) 2 / D
   unsigned* ctrl;
 };
 
