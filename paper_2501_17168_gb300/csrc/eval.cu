@@ -345,37 +345,66 @@ __global__ void __launch_bounds__(NW * 32, K >= 16 ? 2 : 3) eval_kernel(const __
                                             smem_u32(xs + qbase + 4 * lane), (unsigned)XS * 4u,
                                             smem_u32(mo + 4 * lane), smem_u32(stk + 4 * lane), res) != 0;
           }
-          for (int oo = 0; oo < O; ++oo) {
+          if constexpr (!MODI) {
+            // one output: the lane's points inside the data first, then its
+            // squared residuals (or outputs) and the warp sum
+            bool inb[K];
+  #pragma unroll
+            for (int j = 0; j < K; ++j) inb[j] = qbase + pt_index<K>(lane, j) < np;
             float v[K];
-            if (!valid) {
   #pragma unroll
-              for (int j = 0; j < K; ++j) v[j] = __int_as_float(0x7fc00000);
-            } else if (MODI && modi_out) {
-              ld_pts<K>(v, mo + oo * CH + 4 * lane);
-            } else {
-  #pragma unroll
-              for (int j = 0; j < K; ++j) v[j] = oo == 0 ? res[j] : 0.0f;
-            }
+            for (int j = 0; j < K; ++j) v[j] = valid ? res[j] : __int_as_float(0x7fc00000);
             if constexpr (OUT) {
-              float* dst = a.out + (p * O + oo) * a.D + p0;
+              float* dst = a.out + p * a.D + p0;
   #pragma unroll
-              for (int j = 0; j < K; ++j) {
-                const int q = qbase + pt_index<K>(lane, j);
-                if (q < np) dst[q] = v[j];
-              }
+              for (int j = 0; j < K; ++j)
+                if (inb[j]) dst[qbase + pt_index<K>(lane, j)] = v[j];
             } else {
               float yv[K];
-              ld_pts<K>(yv, ys + oo * a.tp + qbase + 4 * lane);
+              ld_pts<K>(yv, ys + qbase + 4 * lane);
               float sse = 0.0f;
   #pragma unroll
               for (int j = 0; j < K; ++j) {
-                const int q = qbase + pt_index<K>(lane, j);
                 const float r = __fsub_rn(v[j], yv[j]);
-                if (q < np) sse = fmaf(r, r, sse);
+                if (inb[j]) sse = fmaf(r, r, sse);
               }
   #pragma unroll
               for (int m = 16; m > 0; m >>= 1) sse += __shfl_xor_sync(0xffffffffu, sse, m);
-              if (lane == 0) cpart[(t * cpt + ch) * O + oo] = valid ? sse : 0.0f;
+              if (lane == 0) cpart[(t * cpt + ch) * O] = valid ? sse : 0.0f;
+            }
+          } else {
+            for (int oo = 0; oo < O; ++oo) {
+              float v[K];
+              if (!valid) {
+  #pragma unroll
+                for (int j = 0; j < K; ++j) v[j] = __int_as_float(0x7fc00000);
+              } else if (MODI && modi_out) {
+                ld_pts<K>(v, mo + oo * CH + 4 * lane);
+              } else {
+  #pragma unroll
+                for (int j = 0; j < K; ++j) v[j] = oo == 0 ? res[j] : 0.0f;
+              }
+              if constexpr (OUT) {
+                float* dst = a.out + (p * O + oo) * a.D + p0;
+  #pragma unroll
+                for (int j = 0; j < K; ++j) {
+                  const int q = qbase + pt_index<K>(lane, j);
+                  if (q < np) dst[q] = v[j];
+                }
+              } else {
+                float yv[K];
+                ld_pts<K>(yv, ys + oo * a.tp + qbase + 4 * lane);
+                float sse = 0.0f;
+  #pragma unroll
+                for (int j = 0; j < K; ++j) {
+                  const int q = qbase + pt_index<K>(lane, j);
+                  const float r = __fsub_rn(v[j], yv[j]);
+                  if (q < np) sse = fmaf(r, r, sse);
+                }
+  #pragma unroll
+                for (int m = 16; m > 0; m >>= 1) sse += __shfl_xor_sync(0xffffffffu, sse, m);
+                if (lane == 0) cpart[(t * cpt + ch) * O + oo] = valid ? sse : 0.0f;
+              }
             }
           }
         }

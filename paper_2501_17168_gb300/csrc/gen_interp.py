@@ -368,7 +368,9 @@ class Gen:
                "r_ma, r_flag, r_t, r_sp, r_sb, r_c, r_cb, r_ct;")
         self.e(".reg .b64 r_cs, r_cb64;")
         self.e("mov.b64 r_cs, 0;")
-        self.e(f".local .align 16 .b8 gm[{MAXS * K * 4}];")
+        # the Modi kernel keeps the NSM shared-memory entries in local memory too
+        n_local = MAXS + (NSM if self.modi else 0)
+        self.e(f".local .align 16 .b8 gm[{n_local * K * 4}];")
         self.e("mov.u32 r_sp, gm;")
         self.e("mov.u32 r_sb, %{sb};")
         self.e("mov.u32 r_ptr, %{pg};")

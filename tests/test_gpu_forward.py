@@ -255,6 +255,18 @@ def test_deep_modi_trees_use_every_stack_level(orc):
     assert len(r["failed"]) == 0 and len(r["class_mismatch"]) == 0, r
 
 
+def test_deepest_modi_trees_fill_the_memory_stack(orc):
+    # full binary Modi trees of 1,023 nodes need 10 levels: three in
+    # registers and all seven memory-stack entries, which the Modi kernel
+    # keeps in local memory
+    p = W.random_population(17, 3, 1023, (1023, 1023), max_depth=9, n_features=2, n_outputs=2,
+                            modi=True, modi_max=12, fset=(0, 1, 2, 3, 4))
+    p = W.stack([p], ld=1024)
+    p = W.Population(p.type, p.val, p.size, 1024)
+    X = np.random.default_rng(13).uniform(-1, 1, (300, 2)).astype(np.float32)
+    check_forward(orc, p, X, O=2)
+
+
 def test_empty_population_and_points():
     p = W.random_population(3, 5, 10, n_features=2)
     X0 = np.zeros((0, 2), np.float32)
