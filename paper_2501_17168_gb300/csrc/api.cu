@@ -25,7 +25,10 @@ const void* adj_finalize_ptr();
 namespace {
 
 constexpr int kMaxDevices = 64;
-constexpr int kNW = 8;
+constexpr int kNW = 8;            // warps per CTA of the plain evaluation kernel
+constexpr int kModiNW = 24;       // of the Modi kernel: one CTA of 24 warps per SM shares
+                                  // its X tile and programs, so the 8 output accumulators
+                                  // of every warp fit beside them
 constexpr int kCtasPerSm = 3;     // resident evaluation CTAs the shape heuristic aims for
 constexpr int kMaxCtasPerSm = 8;  // 2048 threads per SM / 256 per CTA
 constexpr int kMaxGroups = TGP_MAX_PROBLEMS;  // evaluation launches per kernel variant in a batch
@@ -97,12 +100,13 @@ int pcap_of(int max_len) { return (max_len + 2 + 1) & ~1; }
 bool shape_for_k(int K, long long P, long long D, int F, int O, int max_len, const tgp_config* cfg,
                  bool modi, bool mse, const DevInfo& dv, Shape* sh) {
   Shape s{};
-  s.nw = kNW;
+  s.nw = modi ? kModiNW : kNW;
   s.K = K;
   if (s.K != 4 && s.K != 8) return false;
   const int CH = 32 * s.K;
   const int pcap = pcap_of(max_len);
-  s.bt = (cfg && cfg->trees_per_block) ? cfg->trees_per_block : 32;
+  // about 8 sub-items (tree, chunk) per warp and tile
+  s.bt = (cfg && cfg->trees_per_block) ? cfg->trees_per_block : (s.nw > kNW ? 48 : 32);
   if (s.bt < 1 || s.bt > 64) return false;
   const long long Dr = D < 1 ? 1 : D;
   if (cfg && cfg->points_per_tile) {
@@ -123,10 +127,12 @@ bool shape_for_k(int K, long long P, long long D, int F, int O, int max_len, con
   auto bytes = [&]() { return eval_smem_bytes(s.K, s.nw, modi, mse, s.bt, pcap, s.tp, F, O); };
   {
     // three CTAs per SM when that keeps tiles of >= 2 chunks and blocks of
-    // >= 8 trees, else two (wide X tiles, long programs, Modi accumulators)
+    // >= 8 trees, else two (wide X tiles, long programs); one CTA of the
+    // wide Modi kernel
     const Shape s0 = s;
     bool fit = false;
-    for (int ctas = kCtasPerSm; ctas >= 2 && !fit; --ctas) {
+    const int c_hi = s.nw > kNW ? 1 : kCtasPerSm, c_lo = s.nw > kNW ? 1 : 2;
+    for (int ctas = c_hi; ctas >= c_lo && !fit; --ctas) {
       s = s0;
       const size_t per_cta = limit / ctas - 1024;
       const int tp_min = ctas > 2 ? 2 * CH : CH, bt_min = ctas > 2 ? 8 : 4;

@@ -145,7 +145,8 @@ __host__ __device__ inline EvalSmem eval_smem_layout(int K, int nw, bool modi, b
 
 // ----------------------------------------------------------- kernel
 template <int K, int NW, bool MODI, bool OUT>
-__global__ void __launch_bounds__(NW * 32, K >= 16 ? 2 : 3) eval_kernel(const __grid_constant__ EvalBatch b) {
+__global__ void __launch_bounds__(NW * 32, NW >= 16 ? 1 : (K >= 16 ? 2 : 3))
+    eval_kernel(const __grid_constant__ EvalBatch b) {
   extern __shared__ __align__(16) unsigned char smem_all[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int CH = 32 * K;
@@ -458,8 +459,8 @@ struct EvalKernelInfo {
 #define TGP_EVAL_INST(K, NW, M, O) {(const void*)eval_kernel<K, NW, M, O>, K, NW, M, O}
 static const EvalKernelInfo kEvalKernels[] = {
     TGP_EVAL_INST(8, 8, false, false), TGP_EVAL_INST(4, 8, false, false),
-    TGP_EVAL_INST(4, 8, true, false),  TGP_EVAL_INST(8, 8, false, true),
-    TGP_EVAL_INST(4, 8, false, true),  TGP_EVAL_INST(4, 8, true, true),
+    TGP_EVAL_INST(4, 24, true, false), TGP_EVAL_INST(8, 8, false, true),
+    TGP_EVAL_INST(4, 8, false, true),  TGP_EVAL_INST(4, 24, true, true),
 };
 #undef TGP_EVAL_INST
 
