@@ -350,7 +350,7 @@ def run_ours(a, rank, world, local_rank):
             "roofline": {"bound": "alu", "term": term, "achieved": achieved / 1e9,
                          "peak": peak / 1e9, "unit": "Gnode·pt/s", "frac": achieved / peak,
                          "traffic": _profile_traffic(a.workload),
-                         "kernel": "eval_kernel<8,8,plain,mse>",
+                         "kernel": "eval_kernel<8,32,plain,mse>",
                          "kernel_ms": 1e3 * eval_s,
                          "peak_basis": f"{sms} SMs x (FP32 128 / SFU 16 (ex2 32) lanes per clock) at "
                                        f"{sm_max_mhz:.0f} MHz, HBM {hbm_gbs} GB/s ({peak_kind})",
@@ -509,7 +509,7 @@ def part_modi(dev, a, index, peaks):
                     "forward + MSE (all points); forward + adjoint on every 10th point",
         "node_points": units, "steps": steps,
         "ms_forward_mse": ms_f, "node_points_per_s_forward": units / (ms_f / 1e3),
-        "roofline": _roofline(units, t_fp32, t_sfu, t_mem, ms_f, "eval_kernel<4,8,modi,mse> (whole call)",
+        "roofline": _roofline(units, t_fp32, t_sfu, t_mem, ms_f, "eval_kernel<4,24,modi,mse> (whole call)",
                               sms, sm_max_mhz, hbm_gbs, peak_kind),
         "fwd_bwd_points": int(Xs.shape[0]), "ms_fwd_bwd_sample": ms_fb,
         "ms_fwd_bwd_extrapolated_all_points": ms_fb * D / Xs.shape[0],

@@ -25,10 +25,14 @@ const void* adj_finalize_ptr();
 namespace {
 
 constexpr int kMaxDevices = 64;
-constexpr int kNW = 8;            // warps per CTA of the plain evaluation kernel
-constexpr int kModiNW = 24;       // of the Modi kernel: one CTA of 24 warps per SM shares
-                                  // its X tile and programs, so the 8 output accumulators
-                                  // of every warp fit beside them
+// Warps per CTA of the evaluation kernels.  A wide CTA (one per SM) shares
+// its X tile and program area among all its warps, so more warps fit in
+// shared memory: 32 for the plain kernel at 8 points per lane (C2 5.95 ->
+// 5.65 ms against 3 CTAs of 8 warps; 62 registers), 24 for the Modi kernel
+// beside the warps' output accumulators (C5 at 250k points 184 -> 133 ms).
+constexpr int kNW = 8;            // plain kernel at 4 points per lane
+constexpr int kPlainNW = 32;      // plain kernel at 8 points per lane
+constexpr int kModiNW = 24;       // Modi kernel (4 points per lane)
 constexpr int kCtasPerSm = 3;     // resident evaluation CTAs the shape heuristic aims for
 constexpr int kMaxCtasPerSm = 8;  // 2048 threads per SM / 256 per CTA
 constexpr int kMaxGroups = TGP_MAX_PROBLEMS;  // evaluation launches per kernel variant in a batch
@@ -100,13 +104,12 @@ int pcap_of(int max_len) { return (max_len + 2 + 1) & ~1; }
 bool shape_for_k(int K, long long P, long long D, int F, int O, int max_len, const tgp_config* cfg,
                  bool modi, bool mse, const DevInfo& dv, Shape* sh) {
   Shape s{};
-  s.nw = modi ? kModiNW : kNW;
+  s.nw = modi ? kModiNW : (K == 8 ? kPlainNW : kNW);
   s.K = K;
   if (s.K != 4 && s.K != 8) return false;
   const int CH = 32 * s.K;
   const int pcap = pcap_of(max_len);
-  // about 8 sub-items (tree, chunk) per warp and tile
-  s.bt = (cfg && cfg->trees_per_block) ? cfg->trees_per_block : (s.nw > kNW ? 48 : 32);
+  s.bt = (cfg && cfg->trees_per_block) ? cfg->trees_per_block : (s.nw > kNW ? (modi ? 48 : 64) : 32);
   if (s.bt < 1 || s.bt > 64) return false;
   const long long Dr = D < 1 ? 1 : D;
   if (cfg && cfg->points_per_tile) {
@@ -116,10 +119,16 @@ bool shape_for_k(int K, long long P, long long D, int F, int O, int max_len, con
     s.tp = 4 * CH;
     while (s.tp > CH && (long long)(s.tp / 2) >= Dr) s.tp /= 2;
   }
-  const long long target = 4LL * dv.sms;  // enough items to balance a persistent grid
+  // enough items to balance a persistent grid (a wide CTA is one per SM)
+  const long long target = (s.nw > kNW ? 2LL : 4LL) * dv.sms;
   if (!(cfg && cfg->trees_per_block)) {
-    // small problems: fewer trees per block so that every SM gets work
-    while (s.bt > 1 && cdiv(P, s.bt) * cdiv(Dr, s.tp) < target) s.bt /= 2;
+    // small problems: fewer trees per block so that every SM gets work, but
+    // a wide CTA keeps at least half as many (tree, chunk) sub-items per
+    // tile as it has warps (one tree's chunks would leave most of it idle)
+    const long long min_sub = s.nw > kNW ? s.nw / 2 : 1;
+    const long long chunks = cdiv(Dr < s.tp ? Dr : s.tp, CH);
+    while (s.bt > 1 && cdiv(P, s.bt) * cdiv(Dr, s.tp) < target && (s.bt / 2) * chunks >= min_sub)
+      s.bt /= 2;
   }
   // fit shared memory: kCtasPerSm CTAs per SM when the heuristic picks the
   // shape, the per-CTA maximum when the caller does
@@ -127,8 +136,7 @@ bool shape_for_k(int K, long long P, long long D, int F, int O, int max_len, con
   auto bytes = [&]() { return eval_smem_bytes(s.K, s.nw, modi, mse, s.bt, pcap, s.tp, F, O); };
   {
     // three CTAs per SM when that keeps tiles of >= 2 chunks and blocks of
-    // >= 8 trees, else two (wide X tiles, long programs); one CTA of the
-    // wide Modi kernel
+    // >= 8 trees, else two (wide X tiles, long programs); one wide CTA
     const Shape s0 = s;
     bool fit = false;
     const int c_hi = s.nw > kNW ? 1 : kCtasPerSm, c_lo = s.nw > kNW ? 1 : 2;
@@ -136,6 +144,11 @@ bool shape_for_k(int K, long long P, long long D, int F, int O, int max_len, con
       s = s0;
       const size_t per_cta = limit / ctas - 1024;
       const int tp_min = ctas > 2 ? 2 * CH : CH, bt_min = ctas > 2 ? 8 : 4;
+      if (s.nw > kNW) {
+        // a wide CTA keeps its tiles and gives up trees first (Modi C5 at
+        // 250k points: 48 trees x 256 points 144 ms, 40 x 512 133 ms)
+        while (bytes() > per_cta && s.bt > 16 && !(cfg && cfg->trees_per_block)) --s.bt;
+      }
       while (bytes() > per_cta && s.tp > tp_min && !(cfg && cfg->points_per_tile)) s.tp /= 2;
       while (bytes() > per_cta && s.bt > bt_min && !(cfg && cfg->trees_per_block)) --s.bt;
       fit = bytes() <= per_cta;
