@@ -81,7 +81,7 @@ __device__ __forceinline__ void st_lane_pts(float* p, const float (&v)[K]) {
 }
 
 template <int K, int NW, bool MODI, int CAP>
-__global__ void __launch_bounds__(NW * 32, 3) adjoint_kernel(AdjArgs a) {
+__global__ void __launch_bounds__(NW * 32, NW > 8 ? 1 : 3) adjoint_kernel(AdjArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int CH = 32 * K;
@@ -268,8 +268,10 @@ struct AdjKernelInfo {
 
 #define TGP_ADJ_INST(K, NW, M, C) {(const void*)adjoint_kernel<K, NW, M, C>, K, NW, C, M}
 static const AdjKernelInfo kAdjKernels[] = {
-    TGP_ADJ_INST(4, 8, false, 128), TGP_ADJ_INST(4, 8, false, 256), TGP_ADJ_INST(4, 8, false, 1024),
-    TGP_ADJ_INST(4, 8, true, 128),  TGP_ADJ_INST(4, 8, true, 256),  TGP_ADJ_INST(4, 8, true, 1024),
+    TGP_ADJ_INST(4, 28, false, 128), TGP_ADJ_INST(4, 28, false, 256), TGP_ADJ_INST(4, 28, false, 1024),
+    TGP_ADJ_INST(4, 28, true, 128),  TGP_ADJ_INST(4, 28, true, 256),  TGP_ADJ_INST(4, 28, true, 1024),
+    TGP_ADJ_INST(4, 8, false, 128),  TGP_ADJ_INST(4, 8, false, 256),  TGP_ADJ_INST(4, 8, false, 1024),
+    TGP_ADJ_INST(4, 8, true, 128),   TGP_ADJ_INST(4, 8, true, 256),   TGP_ADJ_INST(4, 8, true, 1024),
 };
 #undef TGP_ADJ_INST
 

@@ -633,7 +633,6 @@ tgp_status run_backward(const tgp_population* pop, const tgp_data* data, const f
   q.base = 0;
   tgp_status s = launch_stage(&q, 1, wsb, st, dv, true);
   if (s != TGP_OK) return s;
-  const int nw = 8;
   // the events bracket every adjoint launch of the call: begin before the
   // first variant, end after the last (a single-output call runs both)
   for (int variant = 0; variant < 2; ++variant) {
@@ -642,39 +641,55 @@ tgp_status run_backward(const tgp_population* pop, const tgp_data* data, const f
     const bool first = variant == 0 || O > 1, last = variant == 1;
     // 4 points per lane: at 8 the per-thread tape doubles and the kernel
     // runs 1.5x slower (156 vs 103 ms on the differentiation workload)
-    int cap = 0;
     const int K = 4;
-    const void* fn = find_adj_kernel(K, nw, modi, pop->max_len, &cap);
-    if (!fn) return TGP_ERR_UNSUPPORTED;
-    // Tiles of 512 points amortise the per-(tree, tile) work over 4 chunks
-    // (128 points: 127 ms, 512: 107 ms on the differentiation workload);
-    // smaller when the data has fewer points, or when wide X tiles would
-    // leave fewer than 3 CTAs per SM.  The population is then split into
-    // tree ranges so that the persistent grid gets about 8 items per CTA.
     const bool fixed_tp = cfg && cfg->points_per_tile;
-    int tp = fixed_tp ? cfg->points_per_tile : 512;
-    if (!fixed_tp)
-      while (tp > 32 * K && tp / 2 >= data->n_points) tp /= 2;
+    // One CTA of 28 warps per SM (registers allow 28 at 72 per thread; 3
+    // CTAs of 8 warps hold 24) over 1024-point tiles where its shared
+    // memory fits tiles of at least 256 points (C4: 93.0 -> 85.2 ms), else
+    // 3 CTAs of 8 warps over 512-point tiles.  Tiles of several chunks
+    // amortise the per-(tree, tile) work (128 points: 127 ms, 512: 107 ms
+    // with one item per tile); smaller when the data has fewer points, or
+    // when wide X tiles would leave fewer than 3 CTAs per SM.  The
+    // population is then split into tree ranges so that the persistent grid
+    // gets about 8 items per CTA.
+    int nw = 0, tp = 0, per_sm = 0;
     size_t smem = 0;
-    int per_sm = 0;
-    for (;;) {
-      smem = adj_smem_bytes(K, nw, modi, w.pcap, pop->max_len, tp, data->n_features, O);
-      if (smem > (size_t)dv.smem_optin) {
-        if (fixed_tp || tp <= 32 * K) return TGP_ERR_UNSUPPORTED;
+    const void* fn = nullptr;
+    for (const int cand : {28, 8}) {
+      int cap = 0;
+      fn = find_adj_kernel(K, cand, modi, pop->max_len, &cap);
+      if (!fn) return TGP_ERR_UNSUPPORTED;
+      const bool wide = cand > 8;
+      tp = fixed_tp ? cfg->points_per_tile : (wide ? 1024 : 512);
+      if (!fixed_tp)
+        while (tp > 32 * K && tp / 2 >= data->n_points) tp /= 2;
+      const int tp_floor = wide && !fixed_tp ? 256 : 32 * K;
+      bool ok = false;
+      for (;;) {
+        smem = adj_smem_bytes(K, cand, modi, w.pcap, pop->max_len, tp, data->n_features, O);
+        if (smem > (size_t)dv.smem_optin) {
+          if (fixed_tp || tp <= tp_floor) break;
+          tp /= 2;
+          continue;
+        }
+        if (!ensure_smem(fn, smem)) return TGP_ERR_CUDA;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, cand * 32, smem) != cudaSuccess)
+          return TGP_ERR_CUDA;
+        if (per_sm < 1) break;
+        ok = true;
+        if (wide || fixed_tp || tp <= 32 * K || per_sm >= 3) break;
         tp /= 2;
-        continue;
       }
-      if (!ensure_smem(fn, smem)) return TGP_ERR_CUDA;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nw * 32, smem) != cudaSuccess)
-        return TGP_ERR_CUDA;
-      if (per_sm < 1) return TGP_ERR_UNSUPPORTED;
-      if (fixed_tp || tp <= 32 * K || per_sm >= 3) break;
-      tp /= 2;
+      if (ok) {
+        nw = cand;
+        break;
+      }
     }
+    if (!nw) return TGP_ERR_UNSUPPORTED;
     const long long n_tiles = cdiv(data->n_points, tp);
     const long long slots = (long long)dv.sms * per_sm;
     long long chunks = cdiv(8 * slots, n_tiles);
-    const long long max_chunks = cdiv(pop->pop, 64);  // >= 64 trees (8 per warp) per item
+    const long long max_chunks = cdiv(pop->pop, 8 * nw);  // >= 8 trees per warp per item
     if (chunks > max_chunks) chunks = max_chunks;
     if (chunks < 1) chunks = 1;
     const long long per_chunk = cdiv(pop->pop, chunks);
