@@ -52,8 +52,10 @@ __host__ __device__ inline AdjSmem adj_smem_layout(int K, int nw, bool modi, int
   size_t w = 0;
   L.w_prog = 16; w = al16(16 + (size_t)pcap * 8);
   L.w_cg = w; w = al16(w + (size_t)max_len * 4);
+  // the Modi outputs of the forward; each output's seed of the reverse
+  // overwrites it once read
   L.w_mo = w; w = al16(w + (modi ? (size_t)O * 32 * K * 4 : 0));
-  L.w_sd = w; w = al16(w + (modi ? (size_t)O * 32 * K * 4 : 0));
+  L.w_sd = L.w_mo;
   L.w_g2 = w; w = al16(w + (size_t)O * 4);
   L.w_slot = w; w = al16(w + (size_t)R * 32 * K * 4);  // register-machine slots
   L.per_warp = w;
@@ -270,6 +272,8 @@ struct AdjKernelInfo {
 static const AdjKernelInfo kAdjKernels[] = {
     TGP_ADJ_INST(4, 28, false, 128), TGP_ADJ_INST(4, 28, false, 256), TGP_ADJ_INST(4, 28, false, 1024),
     TGP_ADJ_INST(4, 28, true, 128),  TGP_ADJ_INST(4, 28, true, 256),  TGP_ADJ_INST(4, 28, true, 1024),
+    TGP_ADJ_INST(4, 16, false, 128), TGP_ADJ_INST(4, 16, false, 256), TGP_ADJ_INST(4, 16, false, 1024),
+    TGP_ADJ_INST(4, 16, true, 128),  TGP_ADJ_INST(4, 16, true, 256),  TGP_ADJ_INST(4, 16, true, 1024),
     TGP_ADJ_INST(4, 8, false, 128),  TGP_ADJ_INST(4, 8, false, 256),  TGP_ADJ_INST(4, 8, false, 1024),
     TGP_ADJ_INST(4, 8, true, 128),   TGP_ADJ_INST(4, 8, true, 256),   TGP_ADJ_INST(4, 8, true, 1024),
 };

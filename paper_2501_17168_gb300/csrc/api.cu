@@ -644,9 +644,10 @@ tgp_status run_backward(const tgp_population* pop, const tgp_data* data, const f
     const int K = 4;
     const bool fixed_tp = cfg && cfg->points_per_tile;
     // One CTA of 28 warps per SM (registers allow 28 at 72 per thread; 3
-    // CTAs of 8 warps hold 24) over 1024-point tiles where its shared
-    // memory fits tiles of at least 256 points (C4: 93.0 -> 85.2 ms), else
-    // 3 CTAs of 8 warps over 512-point tiles.  Tiles of several chunks
+    // CTAs of 8 warps hold 24) over tiles of up to 1024 points where its
+    // shared memory fits (C4: 93.0 -> 85.2 ms), else one of 16 warps (Modi
+    // populations: the per-warp output rows), else 3 CTAs of 8 warps over
+    // tiles of up to 512 points.  Tiles of several chunks
     // amortise the per-(tree, tile) work (128 points: 127 ms, 512: 107 ms
     // with one item per tile); smaller when the data has fewer points, or
     // when wide X tiles would leave fewer than 3 CTAs per SM.  The
@@ -655,7 +656,7 @@ tgp_status run_backward(const tgp_population* pop, const tgp_data* data, const f
     int nw = 0, tp = 0, per_sm = 0;
     size_t smem = 0;
     const void* fn = nullptr;
-    for (const int cand : {28, 8}) {
+    for (const int cand : {28, 16, 8}) {
       int cap = 0;
       fn = find_adj_kernel(K, cand, modi, pop->max_len, &cap);
       if (!fn) return TGP_ERR_UNSUPPORTED;
@@ -663,7 +664,7 @@ tgp_status run_backward(const tgp_population* pop, const tgp_data* data, const f
       tp = fixed_tp ? cfg->points_per_tile : (wide ? 1024 : 512);
       if (!fixed_tp)
         while (tp > 32 * K && tp / 2 >= data->n_points) tp /= 2;
-      const int tp_floor = wide && !fixed_tp ? 256 : 32 * K;
+      const int tp_floor = 32 * K;
       bool ok = false;
       for (;;) {
         smem = adj_smem_bytes(K, cand, modi, w.pcap, pop->max_len, tp, data->n_features, O);
