@@ -28,11 +28,13 @@ constexpr int kMaxDevices = 64;
 // Warps per CTA of the evaluation kernels.  A wide CTA (one per SM) shares
 // its X tile and program area among all its warps, so more warps fit in
 // shared memory: 32 for the plain kernel at 8 points per lane (C2 5.95 ->
-// 5.65 ms against 3 CTAs of 8 warps; 62 registers), 24 for the Modi kernel
-// beside the warps' output accumulators (C5 at 250k points 184 -> 133 ms).
-constexpr int kNW = 8;            // plain kernel at 4 points per lane
+// 5.65 ms against 3 CTAs of 8 warps; 62 registers), 28 for the Modi kernel
+// beside the warps' output accumulators (C5 at 250k points 184 -> 130 ms;
+// 72 registers allow 28).  Narrower CTAs (16, then 8 warps) take over
+// where shared memory would cramp the wide one.
+constexpr int kNW = 8;            // the narrow CTA (3 per SM)
 constexpr int kPlainNW = 32;      // plain kernel at 8 points per lane
-constexpr int kModiNW = 24;       // Modi kernel (4 points per lane)
+constexpr int kModiNW = 28;       // Modi kernel (4 points per lane)
 constexpr int kCtasPerSm = 3;     // resident evaluation CTAs the shape heuristic aims for
 constexpr int kMaxCtasPerSm = 8;  // 2048 threads per SM / 256 per CTA
 constexpr int kMaxGroups = TGP_MAX_PROBLEMS;  // evaluation launches per kernel variant in a batch
@@ -101,10 +103,10 @@ int pcap_of(int max_len) { return (max_len + 2 + 1) & ~1; }
 
 // Launch shape for K points per lane: the caller's config where given, else
 // the heuristic.
-bool shape_for_k(int K, long long P, long long D, int F, int O, int max_len, const tgp_config* cfg,
-                 bool modi, bool mse, const DevInfo& dv, Shape* sh) {
+bool shape_for_k(int K, int nw, long long P, long long D, int F, int O, int max_len,
+                 const tgp_config* cfg, bool modi, bool mse, const DevInfo& dv, Shape* sh) {
   Shape s{};
-  s.nw = modi ? kModiNW : (K == 8 ? kPlainNW : kNW);
+  s.nw = nw;
   s.K = K;
   if (s.K != 4 && s.K != 8) return false;
   const int CH = 32 * s.K;
@@ -132,6 +134,7 @@ bool shape_for_k(int K, long long P, long long D, int F, int O, int max_len, con
   }
   // fit shared memory: kCtasPerSm CTAs per SM when the heuristic picks the
   // shape, the per-CTA maximum when the caller does
+  const int bt0 = s.bt, tp0 = s.tp;
   const size_t limit = (size_t)dv.smem_optin;
   auto bytes = [&]() { return eval_smem_bytes(s.K, s.nw, modi, mse, s.bt, pcap, s.tp, F, O); };
   {
@@ -170,8 +173,29 @@ bool shape_for_k(int K, long long P, long long D, int F, int O, int max_len, con
   }
   s.n_groups = (int)cdiv(s.n_tiles, s.g);
   s.n_items = (long long)s.n_blocks * s.n_groups;
+  s.cramped = s.bt < (bt0 < 16 ? bt0 : 16) || s.tp < (tp0 < 2 * CH ? tp0 : 2 * CH);
   *sh = s;
   return true;
+}
+
+// Warps per CTA: the wide CTA for K (one per SM), then narrower ones down to
+// kNW, for as long as shared memory cramps the wider one (many Modi outputs,
+// wide feature sets); nw_cap (0: none) bounds the choice (a batch takes one
+// width per kernel variant).
+bool shape_nw(int K, long long P, long long D, int F, int O, int max_len, const tgp_config* cfg,
+              bool modi, bool mse, const DevInfo& dv, Shape* sh, int nw_cap) {
+  static const int kModiCand[] = {kModiNW, 16, kNW}, kPlainCand[] = {kPlainNW, kNW};
+  const int* cand = modi ? kModiCand : kPlainCand;
+  const int n = modi ? 3 : 2;
+  for (int i = 0; i < n; ++i) {
+    const int nw = (!modi && K != 8) ? kNW : cand[i];
+    if (nw_cap && nw > nw_cap) continue;
+    if (!shape_for_k(K, nw, P, D, F, O, max_len, cfg, modi, mse, dv, sh)) continue;
+    if (!sh->cramped || nw == kNW) return true;
+  }
+  return nw_cap == 0 || nw_cap >= kNW
+             ? shape_for_k(K, kNW, P, D, F, O, max_len, cfg, modi, mse, dv, sh)
+             : false;
 }
 
 // Launch shape: 8 points per lane for single-output populations unless the
@@ -183,14 +207,14 @@ bool shape_for_k(int K, long long P, long long D, int F, int O, int max_len, con
 // lanes idle (60 points: 14% faster with 4 per lane, measured).  A batch
 // keeps 8 so that its problems share one kernel variant.
 bool choose_shape(long long P, long long D, int F, int O, int max_len, const tgp_config* cfg,
-                  bool modi, bool mse, const DevInfo& dv, Shape* sh, bool single) {
-  if (modi) return shape_for_k(4, P, D, F, O, max_len, cfg, modi, mse, dv, sh);
+                  bool modi, bool mse, const DevInfo& dv, Shape* sh, bool single, int nw_cap = 0) {
+  if (modi) return shape_nw(4, P, D, F, O, max_len, cfg, modi, mse, dv, sh, nw_cap);
   if (cfg && cfg->points_per_lane)
-    return shape_for_k(cfg->points_per_lane, P, D, F, O, max_len, cfg, modi, mse, dv, sh);
-  if (single && D <= 32 * 4 && shape_for_k(4, P, D, F, O, max_len, cfg, modi, mse, dv, sh))
+    return shape_nw(cfg->points_per_lane, P, D, F, O, max_len, cfg, modi, mse, dv, sh, nw_cap);
+  if (single && D <= 32 * 4 && shape_nw(4, P, D, F, O, max_len, cfg, modi, mse, dv, sh, nw_cap))
     return true;
-  return shape_for_k(8, P, D, F, O, max_len, cfg, modi, mse, dv, sh) ||
-         shape_for_k(4, P, D, F, O, max_len, cfg, modi, mse, dv, sh);
+  return shape_nw(8, P, D, F, O, max_len, cfg, modi, mse, dv, sh, nw_cap) ||
+         shape_nw(4, P, D, F, O, max_len, cfg, modi, mse, dv, sh, nw_cap);
 }
 
 WsLayout ws_layout(long long P, int max_len, int O, int n_groups) {
@@ -224,12 +248,15 @@ bool data_ok(const tgp_data* d) {
 
 // Shapes of both kernel variants share n_groups so one partial buffer serves.
 bool shapes_for(const tgp_population* pop, const tgp_data* data, int O, const tgp_config* cfg,
-                bool mse, const DevInfo& dv, Shape* plain, Shape* modi, bool single) {
+                bool mse, const DevInfo& dv, Shape* plain, Shape* modi, bool single,
+                int plain_nw_cap = 0, int modi_nw_cap = 0) {
   long long D = data ? data->n_points : 0;
   int F = data ? data->n_features : 1;
-  if (!choose_shape(pop->pop, D, F, O, pop->max_len, cfg, true, mse, dv, modi, single)) return false;
+  if (!choose_shape(pop->pop, D, F, O, pop->max_len, cfg, true, mse, dv, modi, single, modi_nw_cap))
+    return false;
   if (O == 1) {
-    if (!choose_shape(pop->pop, D, F, O, pop->max_len, cfg, false, mse, dv, plain, single))
+    if (!choose_shape(pop->pop, D, F, O, pop->max_len, cfg, false, mse, dv, plain, single,
+                      plain_nw_cap))
       return false;
   } else {
     *plain = *modi;
@@ -252,8 +279,10 @@ struct Planned {
   int flags = 0;    // TGP_FLAG_* of the problem
 };
 
-tgp_status plan(Planned& q, const tgp_config* cfg, bool mse, const DevInfo& dv, bool single) {
-  if (!shapes_for(q.pop, q.data, q.O, cfg, mse, dv, &q.sp, &q.sm, single)) return TGP_ERR_UNSUPPORTED;
+tgp_status plan(Planned& q, const tgp_config* cfg, bool mse, const DevInfo& dv, bool single,
+                int plain_nw_cap = 0, int modi_nw_cap = 0) {
+  if (!shapes_for(q.pop, q.data, q.O, cfg, mse, dv, &q.sp, &q.sm, single, plain_nw_cap, modi_nw_cap))
+    return TGP_ERR_UNSUPPORTED;
   const int n_groups = q.sm.n_groups > q.sp.n_groups ? q.sm.n_groups : q.sp.n_groups;
   q.w = ws_layout(q.pop->pop, q.pop->max_len, q.O, mse ? n_groups : 0);
   for (Shape* sh : {&q.sp, &q.sm}) {
@@ -499,22 +528,41 @@ bool shape_given(const tgp_config& c) {
 tgp_status plan_batch(const tgp_problem* probs, int n, const DevInfo& dv, Planned* qs, size_t* total,
                       const tgp_config* tuned = nullptr) {
   if (n < 1 || n > TGP_MAX_PROBLEMS || !probs) return TGP_ERR_INVALID_ARG;
-  size_t off = al256(CTRL_WORDS * 4);
-  for (int i = 0; i < n; ++i) {
-    const tgp_problem& p = probs[i];
-    if (!problem_ok(&p.pop, &p.data, p.n_outputs)) return TGP_ERR_INVALID_ARG;
-    if (p.data.n_points < 1 || (p.pop.pop > 0 && (!p.y || !p.mse))) return TGP_ERR_INVALID_ARG;
-    if ((p.cfg.flags & ~TGP_FLAG_SSE) != 0) return TGP_ERR_INVALID_ARG;
-    Planned& q = qs[i];
-    q = Planned{&p.pop, &p.data, p.y, p.n_outputs, nullptr, p.mse, p.tree_status};
-    q.flags = p.cfg.flags;
-    const tgp_config* cfg = shape_given(p.cfg) ? &p.cfg
-                            : (tuned && shape_given(tuned[i])) ? &tuned[i]
-                                                                : nullptr;
-    tgp_status s = plan(q, cfg, true, dv, false);
-    if (s != TGP_OK) return s;
-    q.base = off;
-    off = al256(off + q.w.total);
+  size_t off = 0;
+  // one launch per kernel variant runs one CTA width: plan every problem,
+  // and if their widths differ, plan them all again at the narrowest
+  int cap_plain = 0, cap_modi = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    off = al256(CTRL_WORDS * 4);
+    for (int i = 0; i < n; ++i) {
+      const tgp_problem& p = probs[i];
+      if (!problem_ok(&p.pop, &p.data, p.n_outputs)) return TGP_ERR_INVALID_ARG;
+      if (p.data.n_points < 1 || (p.pop.pop > 0 && (!p.y || !p.mse))) return TGP_ERR_INVALID_ARG;
+      if ((p.cfg.flags & ~TGP_FLAG_SSE) != 0) return TGP_ERR_INVALID_ARG;
+      Planned& q = qs[i];
+      q = Planned{&p.pop, &p.data, p.y, p.n_outputs, nullptr, p.mse, p.tree_status};
+      q.flags = p.cfg.flags;
+      const tgp_config* cfg = shape_given(p.cfg) ? &p.cfg
+                              : (tuned && shape_given(tuned[i])) ? &tuned[i]
+                                                                  : nullptr;
+      tgp_status s = plan(q, cfg, true, dv, false, cap_plain, cap_modi);
+      if (s != TGP_OK) return s;
+      q.base = off;
+      off = al256(off + q.w.total);
+    }
+    int lo_plain = 0, hi_plain = 0, lo_modi = 0, hi_modi = 0;
+    for (int i = 0; i < n; ++i) {
+      const int m = qs[i].sm.nw;
+      lo_modi = lo_modi ? (m < lo_modi ? m : lo_modi) : m;
+      hi_modi = m > hi_modi ? m : hi_modi;
+      if (qs[i].O != 1) continue;
+      const int w = qs[i].sp.nw;
+      lo_plain = lo_plain ? (w < lo_plain ? w : lo_plain) : w;
+      hi_plain = w > hi_plain ? w : hi_plain;
+    }
+    if (lo_plain == hi_plain && lo_modi == hi_modi) break;
+    cap_plain = lo_plain;
+    cap_modi = lo_modi;
   }
   // one launch needs one points-per-lane value per kernel variant
   for (int i = 1; i < n; ++i) {

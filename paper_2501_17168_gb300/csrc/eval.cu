@@ -458,9 +458,12 @@ struct EvalKernelInfo {
 
 #define TGP_EVAL_INST(K, NW, M, O) {(const void*)eval_kernel<K, NW, M, O>, K, NW, M, O}
 static const EvalKernelInfo kEvalKernels[] = {
-    TGP_EVAL_INST(8, 32, false, false), TGP_EVAL_INST(4, 8, false, false),
-    TGP_EVAL_INST(4, 24, true, false), TGP_EVAL_INST(8, 32, false, true),
-    TGP_EVAL_INST(4, 8, false, true),  TGP_EVAL_INST(4, 24, true, true),
+    TGP_EVAL_INST(8, 32, false, false), TGP_EVAL_INST(8, 8, false, false),
+    TGP_EVAL_INST(4, 8, false, false),  TGP_EVAL_INST(4, 28, true, false),
+    TGP_EVAL_INST(4, 16, true, false),  TGP_EVAL_INST(4, 8, true, false),
+    TGP_EVAL_INST(8, 32, false, true),  TGP_EVAL_INST(8, 8, false, true),
+    TGP_EVAL_INST(4, 8, false, true),   TGP_EVAL_INST(4, 28, true, true),
+    TGP_EVAL_INST(4, 16, true, true),   TGP_EVAL_INST(4, 8, true, true),
 };
 #undef TGP_EVAL_INST
 

@@ -109,6 +109,7 @@ struct Shape {
   int n_groups;
   int n_blocks;
   long long n_items;
+  bool cramped;  // shared memory forced fewer trees or points than the heuristic wanted
 };
 
 struct StageArgs {

@@ -112,3 +112,36 @@ def test_batch_rejects_bad_arguments():
     assert _lib.load().tgp_batch_workspace_size(None, 1) == 0
     with pytest.raises(_lib.TGPError):
         api.tgp_batch_fitness_mse([bp] * 17)
+
+
+def test_batch_of_mixed_cta_widths(orc):
+    """A launch runs one CTA width per kernel variant.  A Modi problem whose
+    sixteen output rows per warp cramp the wide CTA and a small Modi problem
+    that fits it are planned together at the narrower width; each MSE then
+    matches its own call up to the FP64 summation order of its tiles, and
+    the oracle."""
+    rng = np.random.default_rng(41)
+    wide = W.random_population(42, 60, 63, (5, 63), max_depth=6, n_features=96, n_outputs=16,
+                               modi=True, modi_max=20, fset=(W.ADD, W.SUB, W.MUL, W.SIN))
+    small = W.random_population(43, 50, 31, (5, 31), max_depth=5, n_features=3, n_outputs=2,
+                                modi=True, modi_max=4, fset=(W.ADD, W.MUL, W.COS))
+    cases = [(wide, rng.standard_normal((3000, 96)).astype(np.float32), 16),
+             (small, rng.uniform(-1, 1, (2000, 3)).astype(np.float32), 2)]
+    bps, ys = [], []
+    for p, X, O in cases:
+        y = rng.standard_normal((X.shape[0], O)).astype(np.float32)
+        t, v, s = api.population_to(p, DEV)
+        bps.append(api.BatchProblem(t, v, s, torch.from_numpy(X).to(DEV), torch.from_numpy(y).to(DEV), O,
+                                    max_len=p.max_len))
+        ys.append(y)
+    api.tgp_batch_fitness_mse(bps)
+    torch.cuda.synchronize()
+    api.tgp_check_device_error()
+    for (p, X, O), y, bp in zip(cases, ys, bps):
+        t, v, s, Xd, yd = bp.tensors
+        one, st = api.tgp_fitness_mse(t, v, s, Xd, yd, O, max_len=p.max_len)
+        np.testing.assert_array_equal(bp.status.cpu().numpy(), st.cpu().numpy())
+        np.testing.assert_allclose(bp.mse.cpu().numpy(), one.cpu().numpy(), rtol=1e-12, atol=0)
+        ref, allow, ost = orc.mse(p.type, p.val, p.size, X, y, n_outputs=O, rel_tol=1e-5)
+        r = compare_mse(bp.mse.cpu().numpy(), ref, allow)
+        assert len(r["failed"]) == 0 and len(r["class_mismatch"]) == 0, r
