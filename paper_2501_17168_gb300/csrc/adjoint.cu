@@ -270,8 +270,8 @@ struct AdjKernelInfo {
 
 #define TGP_ADJ_INST(K, NW, M, C) {(const void*)adjoint_kernel<K, NW, M, C>, K, NW, C, M}
 static const AdjKernelInfo kAdjKernels[] = {
-    TGP_ADJ_INST(4, 28, false, 128), TGP_ADJ_INST(4, 28, false, 256), TGP_ADJ_INST(4, 28, false, 1024),
-    TGP_ADJ_INST(4, 28, true, 128),  TGP_ADJ_INST(4, 28, true, 256),  TGP_ADJ_INST(4, 28, true, 1024),
+    TGP_ADJ_INST(4, 32, false, 128), TGP_ADJ_INST(4, 32, false, 256), TGP_ADJ_INST(4, 32, false, 1024),
+    TGP_ADJ_INST(4, 32, true, 128),  TGP_ADJ_INST(4, 32, true, 256),  TGP_ADJ_INST(4, 32, true, 1024),
     TGP_ADJ_INST(4, 16, false, 128), TGP_ADJ_INST(4, 16, false, 256), TGP_ADJ_INST(4, 16, false, 1024),
     TGP_ADJ_INST(4, 16, true, 128),  TGP_ADJ_INST(4, 16, true, 256),  TGP_ADJ_INST(4, 16, true, 1024),
     TGP_ADJ_INST(4, 8, false, 128),  TGP_ADJ_INST(4, 8, false, 256),  TGP_ADJ_INST(4, 8, false, 1024),

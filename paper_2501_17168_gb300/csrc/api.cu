@@ -691,11 +691,11 @@ tgp_status run_backward(const tgp_population* pop, const tgp_data* data, const f
     // runs 1.5x slower (156 vs 103 ms on the differentiation workload)
     const int K = 4;
     const bool fixed_tp = cfg && cfg->points_per_tile;
-    // One CTA of 28 warps per SM (registers allow 28 at 72 per thread; 3
-    // CTAs of 8 warps hold 24) over tiles of up to 1024 points where its
-    // shared memory fits (C4: 93.0 -> 85.2 ms), else one of 16 warps (Modi
-    // populations: the per-warp output rows), else 3 CTAs of 8 warps over
-    // tiles of up to 512 points.  Tiles of several chunks
+    // One CTA of 32 warps per SM (64 registers, no spills; 3 CTAs of 8
+    // warps hold 24) over tiles of up to 1024 points where its shared memory
+    // fits (C4: 93.0 -> 81.9 ms; 28 warps: 85.2 ms), else one of 16 warps
+    // (Modi populations: the per-warp output rows), else 3 CTAs of 8 warps
+    // over tiles of up to 512 points.  Tiles of several chunks
     // amortise the per-(tree, tile) work (128 points: 127 ms, 512: 107 ms
     // with one item per tile); smaller when the data has fewer points, or
     // when wide X tiles would leave fewer than 3 CTAs per SM.  The
@@ -704,7 +704,7 @@ tgp_status run_backward(const tgp_population* pop, const tgp_data* data, const f
     int nw = 0, tp = 0, per_sm = 0;
     size_t smem = 0;
     const void* fn = nullptr;
-    for (const int cand : {28, 16, 8}) {
+    for (const int cand : {32, 16, 8}) {
       int cap = 0;
       fn = find_adj_kernel(K, cand, modi, pop->max_len, &cap);
       if (!fn) return TGP_ERR_UNSUPPORTED;
