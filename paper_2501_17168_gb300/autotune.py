@@ -56,7 +56,8 @@ def _device_key(device, P, D, F, O, max_len) -> str:
 def candidates(P: int, D: int, O: int = 1):
     """The heuristic ({}) plus points per lane x tile widths x tree blocks:
     from one tree per block over wide tiles (the data-parallel schedule) to
-    32 trees per block over one-chunk tiles (the population-parallel one)."""
+    64 trees per block over one-chunk tiles (the population-parallel one;
+    the wide CTAs of 24-32 warps want blocks of 32-64 trees)."""
     out = [{}]  # the library's own shape heuristic
     for K in ((4,) if O > 1 else (8, 4)):
         ch = 32 * K
@@ -64,7 +65,7 @@ def candidates(P: int, D: int, O: int = 1):
             tp = ch * tp_mult
             if tp > 4096 or (tp > ch and tp // 2 >= D):
                 continue
-            for bt in (1, 4, 8, 16, 32):
+            for bt in (1, 4, 8, 16, 32, 64):
                 if bt > P:
                     continue
                 out.append({"points_per_lane": K, "points_per_tile": tp, "trees_per_block": bt})

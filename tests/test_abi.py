@@ -126,13 +126,13 @@ def test_autotune_cache_round_trip_through_the_c_reader(lib, tmp_path):
     assert autotune.lg(100_000) == 17 and autotune.lg(255) == 8 and autotune.lg(181) == 7
     k = autotune.key("NVIDIA GB300", 5000, 100_000, 16, 1, 255)
     assert k == "NVIDIA_GB300|P12_D17_F16_O1_L8"
-    # candidates: the heuristic first, both schedules (1 and 32 trees per
-    # block), tiles that are multiples of a warp's chunk and no wider than
-    # needed, one points-per-lane value for Modi populations
+    # candidates: the heuristic first, both schedules (1 and up to 64 trees
+    # per block), tiles that are multiples of a warp's chunk and no wider
+    # than needed, one points-per-lane value for Modi populations
     c = autotune.candidates(5000, 100_000, 1)
     assert c[0] == {}
     bts = {x["trees_per_block"] for x in c[1:]}
-    assert {1, 32} <= bts
+    assert {1, 32, 64} <= bts
     for x in c[1:]:
         assert x["points_per_tile"] % (32 * x["points_per_lane"]) == 0
         assert x["points_per_tile"] <= 4096
