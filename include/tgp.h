@@ -129,6 +129,13 @@ typedef struct tgp_config {
                                polls, seconds); a negative value gives up at
                                once, which drives the TGP_ERR_TIMEOUT path
                                (tgp_check_device_error) without a fault      */
+  int32_t cta_width;        /* 0 = the library's choice; 1 = CTAs of 8 warps,
+                               several per SM; 2 = one wide CTA per SM (32
+                               warps for the single-output kernel at 8 points
+                               per lane, 28 for the Modi kernel, narrower
+                               where shared memory does not hold it) whose
+                               warps share one X tile and program area; other
+                               values are TGP_ERR_INVALID_ARG                */
 } tgp_config;
 
 /* tgp_config.flags bits. */
@@ -216,7 +223,8 @@ tgp_status tgp_batch_fitness_mse(const tgp_problem* probs, int32_t n, void* ws, 
  *                line ('#' starts a comment):
  *                  <GPU name, spaces as '_'>|P<lg P>_D<lg D>_F<F>_O<O>_L<lg L>
  *                  trees_per_block=<n> points_per_tile=<n> tiles_per_item=<n>
- *                  points_per_lane=<n> [other name=value pairs are ignored]
+ *                  points_per_lane=<n> [cta_width=<0..2>]
+ *                  [other name=value pairs are ignored]
  *                (all on one line; lg x = log2(x) rounded to the nearest
  *                integer).
  *   plan         [host] out: the plan (host memory the library allocates with

@@ -39,7 +39,8 @@ class tgp_config(ctypes.Structure):
     _fields_ = [("trees_per_block", ctypes.c_int32), ("points_per_tile", ctypes.c_int32),
                 ("tiles_per_item", ctypes.c_int32), ("points_per_lane", ctypes.c_int32),
                 ("eval_begin_event", ctypes.c_void_p), ("eval_end_event", ctypes.c_void_p),
-                ("flags", ctypes.c_int32), ("max_wait_polls", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("max_wait_polls", ctypes.c_int32),
+                ("cta_width", ctypes.c_int32)]
 
 
 FLAG_SSE = 1

@@ -82,7 +82,7 @@ def make_config(cfg) -> tgp_config | None:
                       int(cfg.get("tiles_per_item", 0)), int(cfg.get("points_per_lane", 0)),
                       ev0.cuda_event if ev0 is not None else None,
                       ev1.cuda_event if ev1 is not None else None,
-                      flags, int(cfg.get("max_wait_polls", 0)))
+                      flags, int(cfg.get("max_wait_polls", 0)), int(cfg.get("cta_width", 0)))
 
 
 def _cref(c):

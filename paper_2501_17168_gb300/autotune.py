@@ -25,7 +25,7 @@ import math
 import os
 import threading
 
-SHAPE_FIELDS = ("trees_per_block", "points_per_tile", "tiles_per_item", "points_per_lane")
+SHAPE_FIELDS = ("trees_per_block", "points_per_tile", "tiles_per_item", "points_per_lane", "cta_width")
 
 _lock = threading.Lock()
 
@@ -57,7 +57,8 @@ def candidates(P: int, D: int, O: int = 1):
     """The heuristic ({}) plus points per lane x tile widths x tree blocks:
     from one tree per block over wide tiles (the data-parallel schedule) to
     64 trees per block over one-chunk tiles (the population-parallel one;
-    the wide CTAs of 24-32 warps want blocks of 32-64 trees)."""
+    the wide CTAs of 28-32 warps want blocks of 32-64 trees), and at 8 points
+    per lane each block of up to 32 trees also in the narrow CTAs."""
     out = [{}]  # the library's own shape heuristic
     for K in ((4,) if O > 1 else (8, 4)):
         ch = 32 * K
@@ -69,6 +70,10 @@ def candidates(P: int, D: int, O: int = 1):
                 if bt > P:
                     continue
                 out.append({"points_per_lane": K, "points_per_tile": tp, "trees_per_block": bt})
+                if K == 8 and bt <= 32:
+                    # the narrow CTAs (several per SM) against the wide one
+                    out.append({"points_per_lane": K, "points_per_tile": tp, "trees_per_block": bt,
+                                "cta_width": 1})
     return out
 
 

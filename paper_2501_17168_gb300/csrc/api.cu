@@ -35,6 +35,7 @@ constexpr int kMaxDevices = 64;
 constexpr int kNW = 8;            // the narrow CTA (3 per SM)
 constexpr int kPlainNW = 32;      // plain kernel at 8 points per lane
 constexpr int kModiNW = 28;       // Modi kernel (4 points per lane)
+constexpr long long kWideMinPoints = 16384;  // the plain kernel's wide CTA from this many points
 constexpr int kCtasPerSm = 3;     // resident evaluation CTAs the shape heuristic aims for
 constexpr int kMaxCtasPerSm = 8;  // 2048 threads per SM / 256 per CTA
 constexpr int kMaxGroups = TGP_MAX_PROBLEMS;  // evaluation launches per kernel variant in a batch
@@ -187,15 +188,23 @@ bool shape_nw(int K, long long P, long long D, int F, int O, int max_len, const 
   static const int kModiCand[] = {kModiNW, 16, kNW}, kPlainCand[] = {kPlainNW, kNW};
   const int* cand = modi ? kModiCand : kPlainCand;
   const int n = modi ? 3 : 2;
-  for (int i = 0; i < n; ++i) {
-    const int nw = (!modi && K != 8) ? kNW : cand[i];
-    if (nw_cap && nw > nw_cap) continue;
-    if (!shape_for_k(K, nw, P, D, F, O, max_len, cfg, modi, mse, dv, sh)) continue;
-    if (!sh->cramped || nw == kNW) return true;
+  const int width = cfg ? cfg->cta_width : 0;  // 0 choose, 1 narrow, 2 wide
+  // The single-output kernel takes the wide CTA for large data sets only: on
+  // a few thousand points the narrow CTAs, several per SM, overlap one
+  // another's program staging and tile barriers (10,000 trees x 1,024
+  // points: 0.55 vs 0.62 ms; x 4,096: 1.92 vs 2.05 ms; 100,000 x 20,640:
+  // 91.0 vs 88.9 ms; C2 at 100,000 points: 5.94 vs 5.64 ms).
+  const bool wide_ok = modi || width == 2 || D >= kWideMinPoints;
+  if (width != 1 && wide_ok) {
+    for (int i = 0; i < n; ++i) {
+      const int nw = (!modi && K != 8) ? kNW : cand[i];
+      if (nw == kNW || (nw_cap && nw > nw_cap)) continue;
+      if (!shape_for_k(K, nw, P, D, F, O, max_len, cfg, modi, mse, dv, sh)) continue;
+      // a caller who asks for the wide CTA takes the widest that fits
+      if (!sh->cramped || width == 2) return true;
+    }
   }
-  return nw_cap == 0 || nw_cap >= kNW
-             ? shape_for_k(K, kNW, P, D, F, O, max_len, cfg, modi, mse, dv, sh)
-             : false;
+  return shape_for_k(K, kNW, P, D, F, O, max_len, cfg, modi, mse, dv, sh);
 }
 
 // Launch shape: 8 points per lane for single-output populations unless the
@@ -490,7 +499,8 @@ tgp_status run(const tgp_population* pop, const tgp_data* data, const float* y, 
   if (!mse && pop->pop > 0 && data->n_points > 0 && !out) return TGP_ERR_INVALID_ARG;
   DevInfo dv;
   if (!dev_info(&dv)) return TGP_ERR_CUDA;
-  if (cfg && (cfg->flags & ~TGP_FLAG_SSE) != 0) return TGP_ERR_INVALID_ARG;
+  if (cfg && ((cfg->flags & ~TGP_FLAG_SSE) != 0 || cfg->cta_width < 0 || cfg->cta_width > 2))
+    return TGP_ERR_INVALID_ARG;
   Planned q{pop, data, y, O, out, mse_out, tree_status};
   q.base = 0;
   q.flags = cfg ? cfg->flags : 0;
@@ -520,7 +530,7 @@ tgp_status run(const tgp_population* pop, const tgp_data* data, const float* y, 
 // finalize launch.  Workspace: a 256-byte control block (the shared work
 // counters) followed by one region per problem.
 bool shape_given(const tgp_config& c) {
-  return c.trees_per_block || c.points_per_tile || c.tiles_per_item || c.points_per_lane;
+  return c.trees_per_block || c.points_per_tile || c.tiles_per_item || c.points_per_lane || c.cta_width;
 }
 
 // tuned: NULL, or per problem a shape to use when the problem's own cfg gives
@@ -538,7 +548,8 @@ tgp_status plan_batch(const tgp_problem* probs, int n, const DevInfo& dv, Planne
       const tgp_problem& p = probs[i];
       if (!problem_ok(&p.pop, &p.data, p.n_outputs)) return TGP_ERR_INVALID_ARG;
       if (p.data.n_points < 1 || (p.pop.pop > 0 && (!p.y || !p.mse))) return TGP_ERR_INVALID_ARG;
-      if ((p.cfg.flags & ~TGP_FLAG_SSE) != 0) return TGP_ERR_INVALID_ARG;
+      if ((p.cfg.flags & ~TGP_FLAG_SSE) != 0 || p.cfg.cta_width < 0 || p.cfg.cta_width > 2)
+        return TGP_ERR_INVALID_ARG;
       Planned& q = qs[i];
       q = Planned{&p.pop, &p.data, p.y, p.n_outputs, nullptr, p.mse, p.tree_status};
       q.flags = p.cfg.flags;
@@ -641,9 +652,10 @@ void cache_read(const char* path, char (*keys)[320], int n, tgp_config* out, int
                      : std::strcmp(tok, "points_per_tile") == 0 ? &c.points_per_tile
                      : std::strcmp(tok, "tiles_per_item") == 0  ? &c.tiles_per_item
                      : std::strcmp(tok, "points_per_lane") == 0 ? &c.points_per_lane
+                     : std::strcmp(tok, "cta_width") == 0       ? &c.cta_width
                                                                 : nullptr;
       if (!dst) continue;
-      if (!num || v < 0 || v > 65536) ok = false;
+      if (!num || v < 0 || v > 65536 || (dst == &c.cta_width && v > 2)) ok = false;
       else *dst = (int32_t)v;
     }
     // Every line for a key replaces the earlier one; a malformed line drops it.
@@ -948,6 +960,7 @@ tgp_status tgp_batch_plan(const tgp_problem* probs, int32_t n, const char* tune_
     c.points_per_tile = sh.tp;
     c.tiles_per_item = sh.g;
     c.points_per_lane = sh.K;
+    c.cta_width = sh.nw > kNW ? 2 : 1;
     c.flags = pl->probs[i].cfg.flags;
     pl->shape[i] = c;
   }

@@ -54,14 +54,16 @@ int main(void) {
     fprintf(f, "GPU_X|P13_D17_F16_O1_L8 trees_per_block=8 points_per_tile=512 tiles_per_item=2 "
                "points_per_lane=8 ms=1.5\n");
     fprintf(f, "GPU_X|P13_D17_F16_O1_L8 trees_per_block=28 points_per_tile=1024 tiles_per_item=0 "
-               "points_per_lane=8\n");
+               "points_per_lane=8 cta_width=2\n");
+    fprintf(f, "GPU_X|P11_D11_F4_O1_L6 trees_per_block=8 cta_width=3\n");
     fprintf(f, "GPU_X|P10_D10_F4_O1_L6 trees_per_block=x\n");
     fclose(f);
     tgp_config c;
     memset(&c, 0, sizeof c);
     CHECK(tgp_tune_cache_lookup(path, "GPU_X|P13_D17_F16_O1_L8", &c) == TGP_OK);
     CHECK(c.trees_per_block == 28 && c.points_per_tile == 1024 && c.tiles_per_item == 0 &&
-          c.points_per_lane == 8 && c.flags == 0);
+          c.points_per_lane == 8 && c.cta_width == 2 && c.flags == 0);
+    CHECK(tgp_tune_cache_lookup(path, "GPU_X|P11_D11_F4_O1_L6", &c) == TGP_ERR_INVALID_ARG);
     CHECK(tgp_tune_cache_lookup(path, "GPU_X|P10_D10_F4_O1_L6", &c) == TGP_ERR_INVALID_ARG);
     CHECK(tgp_tune_cache_lookup(path, "GPU_Y|P13_D17_F16_O1_L8", &c) == TGP_ERR_INVALID_ARG);
     CHECK(tgp_tune_cache_lookup("no_such_file.txt", "GPU_X|P13_D17_F16_O1_L8", &c) ==

@@ -141,6 +141,8 @@ def test_autotune_cache_round_trip_through_the_c_reader(lib, tmp_path):
     assert all(x["points_per_tile"] // 2 < 100 or x["points_per_tile"] == 32 * x["points_per_lane"]
                for x in small[1:])
     assert {x["points_per_lane"] for x in autotune.candidates(100, 1000, 8)[1:]} == {4}
+    assert {x.get("cta_width", 0) for x in c[1:] if x["points_per_lane"] == 8} == {0, 1}
+    assert all(x.get("cta_width", 0) == 0 for x in autotune.candidates(100, 1000, 8)[1:])
     path = str(tmp_path / "tune.txt")
     autotune.store({k: ({"trees_per_block": 8, "points_per_tile": 512, "points_per_lane": 8}, 2.0)}, path)
     autotune.store({k: ({"trees_per_block": 28, "points_per_tile": 1024, "tiles_per_item": 3,

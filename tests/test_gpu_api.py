@@ -195,3 +195,33 @@ def test_batch_plan_without_cache_equals_one_shot_batch():
     torch.cuda.synchronize()
     for a, bp in zip(first, bps):
         assert _bits_equal(a, bp.mse)
+
+
+def test_cta_width_option(orc):
+    """cta_width picks the narrow CTAs (1) or one wide CTA per SM (2) for the
+    single-output and the Modi kernel: the per-point outputs are the same
+    bits (same interpreter, same points per lane), the MSE agrees up to the
+    FP64 summation order of the tiles, and other values are refused."""
+    p, X, y, (t, v, s, Xd, yd) = _problem(seed=21, P=200, D=6000)
+    outs, mses = [], []
+    for w in (0, 1, 2):
+        o, _ = api.tgp_eval_forward(t, v, s, Xd, 1, max_len=p.max_len, config={"cta_width": w})
+        m, st = api.tgp_fitness_mse(t, v, s, Xd, yd, 1, max_len=p.max_len, config={"cta_width": w})
+        outs.append(o)
+        mses.append(m.cpu().numpy())
+    assert _bits_equal(outs[0], outs[1]) and _bits_equal(outs[0], outs[2])
+    np.testing.assert_allclose(mses[1], mses[0], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(mses[2], mses[0], rtol=1e-12, atol=0)
+    m = W.random_population(22, 80, 63, (9, 63), max_depth=6, n_features=6, n_outputs=3, modi=True,
+                            modi_max=6)
+    tm, vm, sm = api.population_to(m, DEV)
+    y3 = torch.from_numpy(np.random.default_rng(23).standard_normal((6000, 3)).astype(np.float32)).to(DEV)
+    got = [api.tgp_fitness_mse(tm, vm, sm, Xd, y3, 3, max_len=63, config={"cta_width": w})[0].cpu().numpy()
+           for w in (1, 2)]
+    np.testing.assert_allclose(got[1], got[0], rtol=1e-12, atol=0)
+    ref, allow, _ = orc.mse(m.type, m.val, m.size, X, y3.cpu().numpy(), n_outputs=3, rel_tol=1e-5)
+    r = compare_mse(got[1], ref, allow)
+    assert len(r["failed"]) == 0 and len(r["class_mismatch"]) == 0, r
+    with pytest.raises(_lib.TGPError) as e:
+        api.tgp_fitness_mse(t, v, s, Xd, yd, 1, max_len=p.max_len, config={"cta_width": 3})
+    assert e.value.code == _lib.TGP_ERR_INVALID_ARG
