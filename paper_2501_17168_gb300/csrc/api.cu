@@ -181,10 +181,9 @@ bool shape_for_k(int K, int nw, long long P, long long D, int F, int O, int max_
 
 // Warps per CTA: the wide CTA for K (one per SM), then narrower ones down to
 // kNW, for as long as shared memory cramps the wider one (many Modi outputs,
-// wide feature sets); nw_cap (0: none) bounds the choice (a batch takes one
-// width per kernel variant).
+// wide feature sets).
 bool shape_nw(int K, long long P, long long D, int F, int O, int max_len, const tgp_config* cfg,
-              bool modi, bool mse, const DevInfo& dv, Shape* sh, int nw_cap) {
+              bool modi, bool mse, const DevInfo& dv, Shape* sh) {
   static const int kModiCand[] = {kModiNW, 16, kNW}, kPlainCand[] = {kPlainNW, kNW};
   const int* cand = modi ? kModiCand : kPlainCand;
   const int n = modi ? 3 : 2;
@@ -198,7 +197,7 @@ bool shape_nw(int K, long long P, long long D, int F, int O, int max_len, const 
   if (width != 1 && wide_ok) {
     for (int i = 0; i < n; ++i) {
       const int nw = (!modi && K != 8) ? kNW : cand[i];
-      if (nw == kNW || (nw_cap && nw > nw_cap)) continue;
+      if (nw == kNW) continue;
       if (!shape_for_k(K, nw, P, D, F, O, max_len, cfg, modi, mse, dv, sh)) continue;
       // a caller who asks for the wide CTA takes the widest that fits
       if (!sh->cramped || width == 2) return true;
@@ -213,17 +212,18 @@ bool shape_nw(int K, long long P, long long D, int F, int O, int max_len, const 
 // memory, and the Modi interpreter at 8 points per lane no longer fits the
 // instruction cache: 2.6x slower, measured).  A single problem of at most
 // 128 points also takes 4: a warp's 256 slots at 8 per lane would leave most
-// lanes idle (60 points: 14% faster with 4 per lane, measured).  A batch
-// keeps 8 so that its problems share one kernel variant.
+// lanes idle (60 points: 14% faster with 4 per lane, measured).  Problems
+// of a batch get the shapes they would get alone (a batch launches one
+// kernel per points-per-lane value and CTA width).
 bool choose_shape(long long P, long long D, int F, int O, int max_len, const tgp_config* cfg,
-                  bool modi, bool mse, const DevInfo& dv, Shape* sh, bool single, int nw_cap = 0) {
-  if (modi) return shape_nw(4, P, D, F, O, max_len, cfg, modi, mse, dv, sh, nw_cap);
+                  bool modi, bool mse, const DevInfo& dv, Shape* sh) {
+  if (modi) return shape_nw(4, P, D, F, O, max_len, cfg, modi, mse, dv, sh);
   if (cfg && cfg->points_per_lane)
-    return shape_nw(cfg->points_per_lane, P, D, F, O, max_len, cfg, modi, mse, dv, sh, nw_cap);
-  if (single && D <= 32 * 4 && shape_nw(4, P, D, F, O, max_len, cfg, modi, mse, dv, sh, nw_cap))
+    return shape_nw(cfg->points_per_lane, P, D, F, O, max_len, cfg, modi, mse, dv, sh);
+  if (D <= 32 * 4 && shape_nw(4, P, D, F, O, max_len, cfg, modi, mse, dv, sh))
     return true;
-  return shape_nw(8, P, D, F, O, max_len, cfg, modi, mse, dv, sh, nw_cap) ||
-         shape_nw(4, P, D, F, O, max_len, cfg, modi, mse, dv, sh, nw_cap);
+  return shape_nw(8, P, D, F, O, max_len, cfg, modi, mse, dv, sh) ||
+         shape_nw(4, P, D, F, O, max_len, cfg, modi, mse, dv, sh);
 }
 
 WsLayout ws_layout(long long P, int max_len, int O, int n_groups) {
@@ -257,15 +257,12 @@ bool data_ok(const tgp_data* d) {
 
 // Shapes of both kernel variants share n_groups so one partial buffer serves.
 bool shapes_for(const tgp_population* pop, const tgp_data* data, int O, const tgp_config* cfg,
-                bool mse, const DevInfo& dv, Shape* plain, Shape* modi, bool single,
-                int plain_nw_cap = 0, int modi_nw_cap = 0) {
+                bool mse, const DevInfo& dv, Shape* plain, Shape* modi) {
   long long D = data ? data->n_points : 0;
   int F = data ? data->n_features : 1;
-  if (!choose_shape(pop->pop, D, F, O, pop->max_len, cfg, true, mse, dv, modi, single, modi_nw_cap))
-    return false;
+  if (!choose_shape(pop->pop, D, F, O, pop->max_len, cfg, true, mse, dv, modi)) return false;
   if (O == 1) {
-    if (!choose_shape(pop->pop, D, F, O, pop->max_len, cfg, false, mse, dv, plain, single,
-                      plain_nw_cap))
+    if (!choose_shape(pop->pop, D, F, O, pop->max_len, cfg, false, mse, dv, plain))
       return false;
   } else {
     *plain = *modi;
@@ -288,10 +285,8 @@ struct Planned {
   int flags = 0;    // TGP_FLAG_* of the problem
 };
 
-tgp_status plan(Planned& q, const tgp_config* cfg, bool mse, const DevInfo& dv, bool single,
-                int plain_nw_cap = 0, int modi_nw_cap = 0) {
-  if (!shapes_for(q.pop, q.data, q.O, cfg, mse, dv, &q.sp, &q.sm, single, plain_nw_cap, modi_nw_cap))
-    return TGP_ERR_UNSUPPORTED;
+tgp_status plan(Planned& q, const tgp_config* cfg, bool mse, const DevInfo& dv) {
+  if (!shapes_for(q.pop, q.data, q.O, cfg, mse, dv, &q.sp, &q.sm)) return TGP_ERR_UNSUPPORTED;
   const int n_groups = q.sm.n_groups > q.sp.n_groups ? q.sm.n_groups : q.sp.n_groups;
   q.w = ws_layout(q.pop->pop, q.pop->max_len, q.O, mse ? n_groups : 0);
   for (Shape* sh : {&q.sp, &q.sm}) {
@@ -374,22 +369,21 @@ tgp_status launch_eval(Planned* qs, int n, char* ws, unsigned* counters, cudaStr
     if (!modi && !any_single) continue;
     int occ[TGP_MAX_PROBLEMS];
     size_t sbytes[TGP_MAX_PROBLEMS];
-    int K = 0, nw = 0;
+    const void* fns[TGP_MAX_PROBLEMS];  // each problem's kernel (points per lane, CTA width)
+    int nws[TGP_MAX_PROBLEMS];
     for (int i = 0; i < n; ++i) {
       occ[i] = 0;
+      fns[i] = nullptr;
       const Planned& q = qs[i];
       if (q.pop->pop == 0 || q.data->n_points == 0) continue;
       if (!modi && q.O > 1) continue;
       const Shape& sh = modi ? q.sm : q.sp;
-      if (K && (sh.K != K || sh.nw != nw)) return TGP_ERR_UNSUPPORTED;
-      K = sh.K;
-      nw = sh.nw;
       sbytes[i] = eval_smem_bytes(sh.K, sh.nw, modi, mse, sh.bt, q.w.pcap, sh.tp, q.data->n_features, q.O);
       if (sbytes[i] > limit) return TGP_ERR_UNSUPPORTED;
-      const void* fn = find_eval_kernel(K, nw, modi, !mse);
+      const void* fn = find_eval_kernel(sh.K, sh.nw, modi, !mse);
       if (!fn) return TGP_ERR_UNSUPPORTED;
       if (!ensure_smem(fn, sbytes[i])) return TGP_ERR_CUDA;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[i], fn, nw * 32, sbytes[i]) != cudaSuccess)
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[i], fn, sh.nw * 32, sbytes[i]) != cudaSuccess)
         return TGP_ERR_CUDA;
       if (occ[i] < 1) return TGP_ERR_UNSUPPORTED;
       if (occ[i] > kMaxCtasPerSm) occ[i] = kMaxCtasPerSm;
@@ -397,18 +391,28 @@ tgp_status launch_eval(Planned* qs, int n, char* ws, unsigned* counters, cudaStr
       // for it (a larger shared-memory carve-out leaves less L1 for the
       // others, so problems are not mixed across carve-out steps)
       occ[i] = occ[i] * 16 + carveout_step((size_t)occ[i] * (sbytes[i] + 1024));
+      fns[i] = fn;
+      nws[i] = sh.nw;
     }
-    if (K == 0) continue;
-    const void* fn = find_eval_kernel(K, nw, modi, !mse);
+    // one launch per (kernel, group key): problems of different points per
+    // lane or CTA width run as separate persistent launches, each problem in
+    // the shape it would get alone
     int ngroup = 0;
     for (int key = kMaxCtasPerSm * 16 + 15; key >= 16; --key) {
+     for (int lead = 0; lead < n; ++lead) {
+      if (!fns[lead] || occ[lead] != key) continue;
+      bool seen = false;  // this kernel's group of this key launched already
+      for (int j = 0; j < lead; ++j) seen |= fns[j] == fns[lead] && occ[j] == key;
+      if (seen) continue;
+      const void* fn = fns[lead];
+      const int nw = nws[lead];
       EvalBatch b{};
       const int per_sm = key / 16;
       long long total = 0;
       size_t smem = 0;
       int m = 0;
       for (int i = 0; i < n; ++i) {
-        if (occ[i] != key) continue;
+        if (occ[i] != key || fns[i] != fn) continue;
         const Planned& q = qs[i];
         const Shape& sh = modi ? q.sm : q.sp;
         char* w = ws + q.base;
@@ -452,6 +456,7 @@ tgp_status launch_eval(Planned* qs, int n, char* ws, unsigned* counters, cudaStr
       void* args[] = {&b};
       if (cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(nw * 32), args, smem, st) != cudaSuccess)
         return TGP_ERR_CUDA;
+     }
     }
   }
   return TGP_OK;
@@ -504,7 +509,7 @@ tgp_status run(const tgp_population* pop, const tgp_data* data, const float* y, 
   Planned q{pop, data, y, O, out, mse_out, tree_status};
   q.base = 0;
   q.flags = cfg ? cfg->flags : 0;
-  tgp_status s = plan(q, cfg, mse, dv, true);
+  tgp_status s = plan(q, cfg, mse, dv);
   if (s != TGP_OK) return s;
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < q.w.total) return TGP_ERR_WORKSPACE;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -538,46 +543,23 @@ bool shape_given(const tgp_config& c) {
 tgp_status plan_batch(const tgp_problem* probs, int n, const DevInfo& dv, Planned* qs, size_t* total,
                       const tgp_config* tuned = nullptr) {
   if (n < 1 || n > TGP_MAX_PROBLEMS || !probs) return TGP_ERR_INVALID_ARG;
-  size_t off = 0;
-  // one launch per kernel variant runs one CTA width: plan every problem,
-  // and if their widths differ, plan them all again at the narrowest
-  int cap_plain = 0, cap_modi = 0;
-  for (int pass = 0; pass < 2; ++pass) {
-    off = al256(CTRL_WORDS * 4);
-    for (int i = 0; i < n; ++i) {
-      const tgp_problem& p = probs[i];
-      if (!problem_ok(&p.pop, &p.data, p.n_outputs)) return TGP_ERR_INVALID_ARG;
-      if (p.data.n_points < 1 || (p.pop.pop > 0 && (!p.y || !p.mse))) return TGP_ERR_INVALID_ARG;
-      if ((p.cfg.flags & ~TGP_FLAG_SSE) != 0 || p.cfg.cta_width < 0 || p.cfg.cta_width > 2)
-        return TGP_ERR_INVALID_ARG;
-      Planned& q = qs[i];
-      q = Planned{&p.pop, &p.data, p.y, p.n_outputs, nullptr, p.mse, p.tree_status};
-      q.flags = p.cfg.flags;
-      const tgp_config* cfg = shape_given(p.cfg) ? &p.cfg
-                              : (tuned && shape_given(tuned[i])) ? &tuned[i]
-                                                                  : nullptr;
-      tgp_status s = plan(q, cfg, true, dv, false, cap_plain, cap_modi);
-      if (s != TGP_OK) return s;
-      q.base = off;
-      off = al256(off + q.w.total);
-    }
-    int lo_plain = 0, hi_plain = 0, lo_modi = 0, hi_modi = 0;
-    for (int i = 0; i < n; ++i) {
-      const int m = qs[i].sm.nw;
-      lo_modi = lo_modi ? (m < lo_modi ? m : lo_modi) : m;
-      hi_modi = m > hi_modi ? m : hi_modi;
-      if (qs[i].O != 1) continue;
-      const int w = qs[i].sp.nw;
-      lo_plain = lo_plain ? (w < lo_plain ? w : lo_plain) : w;
-      hi_plain = w > hi_plain ? w : hi_plain;
-    }
-    if (lo_plain == hi_plain && lo_modi == hi_modi) break;
-    cap_plain = lo_plain;
-    cap_modi = lo_modi;
-  }
-  // one launch needs one points-per-lane value per kernel variant
-  for (int i = 1; i < n; ++i) {
-    if (qs[i].O == 1 && qs[0].O == 1 && qs[i].sp.K != qs[0].sp.K) return TGP_ERR_UNSUPPORTED;
+  size_t off = al256(CTRL_WORDS * 4);
+  for (int i = 0; i < n; ++i) {
+    const tgp_problem& p = probs[i];
+    if (!problem_ok(&p.pop, &p.data, p.n_outputs)) return TGP_ERR_INVALID_ARG;
+    if (p.data.n_points < 1 || (p.pop.pop > 0 && (!p.y || !p.mse))) return TGP_ERR_INVALID_ARG;
+    if ((p.cfg.flags & ~TGP_FLAG_SSE) != 0 || p.cfg.cta_width < 0 || p.cfg.cta_width > 2)
+      return TGP_ERR_INVALID_ARG;
+    Planned& q = qs[i];
+    q = Planned{&p.pop, &p.data, p.y, p.n_outputs, nullptr, p.mse, p.tree_status};
+    q.flags = p.cfg.flags;
+    const tgp_config* cfg = shape_given(p.cfg) ? &p.cfg
+                            : (tuned && shape_given(tuned[i])) ? &tuned[i]
+                                                                : nullptr;
+    tgp_status s = plan(q, cfg, true, dv);
+    if (s != TGP_OK) return s;
+    q.base = off;
+    off = al256(off + q.w.total);
   }
   *total = off;
   return TGP_OK;
@@ -678,7 +660,7 @@ tgp_status run_backward(const tgp_population* pop, const tgp_data* data, const f
   DevInfo dv;
   if (!dev_info(&dv)) return TGP_ERR_CUDA;
   Shape sp, sm;
-  if (!shapes_for(pop, data, O, nullptr, true, dv, &sp, &sm, true)) return TGP_ERR_UNSUPPORTED;
+  if (!shapes_for(pop, data, O, nullptr, true, dv, &sp, &sm)) return TGP_ERR_UNSUPPORTED;
   const int n_groups = sm.n_groups > sp.n_groups ? sm.n_groups : sp.n_groups;
   WsLayout w = ws_layout(pop->pop, pop->max_len, O, n_groups);
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < w.total) return TGP_ERR_WORKSPACE;
@@ -839,7 +821,7 @@ size_t tgp_workspace_size(const tgp_population* pop, const tgp_data* data, int32
   int n_groups = 0;
   if (data && data->n_points > 0) {
     Shape sp, sm;
-    if (!shapes_for(pop, data, n_outputs, cfg, true, dv, &sp, &sm, true)) return 0;
+    if (!shapes_for(pop, data, n_outputs, cfg, true, dv, &sp, &sm)) return 0;
     n_groups = sm.n_groups > sp.n_groups ? sm.n_groups : sp.n_groups;
   }
   return ws_layout(pop->pop, pop->max_len, n_outputs, n_groups).total;

@@ -21,20 +21,26 @@ namespace tgp {
 struct NodeSmem {
   uint32_t* info;   // bits 0-3 func, 4-6 kind (0 var, 1 const, 2 unary, 3 binary, 4 ternary),
                     // 7 modi, 8-15 out, 16 scratch of the compiler
-  uint32_t* leaf;   // variable index or constant bits
   int16_t* sz;      // subtree size (0 = not a valid size)
   int16_t* par;     // parent index
   uint8_t* need;    // registers (levels) the subtree needs
   uint8_t* slot;    // the subtree's level (first free slot for the adjoint set)
+  const float* V;   // the tree's value row in global memory (read again for
+                    // leaf operands: 10 bytes per node in shared memory
+                    // instead of 14 let more trees compile at once)
+  // a validated leaf's operand: variable index or constant bits
+  __device__ __forceinline__ uint32_t leaf(int i) const {
+    const float v = __ldg(V + i);
+    return (info[i] >> 4 & 7) == 0 ? (uint32_t)v : __float_as_uint(v);
+  }
 };
 
-__host__ __device__ constexpr size_t node_smem_bytes(int lmax) { return (size_t)lmax * 14; }
+__host__ __device__ constexpr size_t node_smem_bytes(int lmax) { return (size_t)lmax * 10; }
 
 __device__ NodeSmem node_smem(unsigned char* base, int lmax) {
   NodeSmem ns;
   ns.info = reinterpret_cast<uint32_t*>(base);
-  ns.leaf = ns.info + lmax;
-  ns.sz = reinterpret_cast<int16_t*>(ns.leaf + lmax);
+  ns.sz = reinterpret_cast<int16_t*>(ns.info + lmax);
   ns.par = ns.sz + lmax;
   ns.need = reinterpret_cast<uint8_t*>(ns.par + lmax);
   ns.slot = ns.need + lmax;
@@ -86,7 +92,7 @@ __device__ int compile_fx(NodeSmem& ns, bool single_out, uint2* prog, int cap) {
     if (down) {
       const int lv = ns.slot[n];
       if (k <= 1) {  // a lone leaf: the root, or the first operand of a Modi node
-        if (!put((k == 0 ? LDV : LDC) + lv, ns.leaf[n])) return -1;
+        if (!put((k == 0 ? LDV : LDC) + lv, ns.leaf(n))) return -1;
         down = false;
         continue;
       }
@@ -97,7 +103,7 @@ __device__ int compile_fx(NodeSmem& ns, bool single_out, uint2* prog, int cap) {
         const int c = n + 1, ck = kind_of(ns.info[c]);
         if (ck <= 1) {  // unary of a leaf: one instruction
           const uint32_t base = modi ? (ck == 0 ? UNV_M : UNC_M) : (ck == 0 ? UNV : UNC);
-          if (!put((base + (f - F_SIN) * NREG + lv) | o16, ns.leaf[c])) return -1;
+          if (!put((base + (f - F_SIN) * NREG + lv) | o16, ns.leaf(c))) return -1;
           down = false;
           continue;
         }
@@ -110,7 +116,7 @@ __device__ int compile_fx(NodeSmem& ns, bool single_out, uint2* prog, int cap) {
         // the condition stack and the branches follow as a binary form
         const int a = n + 1, ka = kind_of(ns.info[a]);
         if (ka <= 1) {
-          if (cdepth >= MAXC || !put((ka == 0 ? CDV : CDC) + lv, ns.leaf[a])) return -1;
+          if (cdepth >= MAXC || !put((ka == 0 ? CDV : CDC) + lv, ns.leaf(a))) return -1;
           ++cdepth;
           ns.info[n] = in | COND_DONE;
           continue;
@@ -124,7 +130,7 @@ __device__ int compile_fx(NodeSmem& ns, bool single_out, uint2* prog, int cap) {
       bin_ops(ns, n, &ca, &cb);
       const int ka = kind_of(ns.info[ca]), kb = kind_of(ns.info[cb]);
       if (ka <= 1 && kb <= 1 && !modi) {  // two leaves: one instruction
-        const uint32_t la = ns.leaf[ca], lb = ns.leaf[cb];
+        const uint32_t la = ns.leaf(ca), lb = ns.leaf(cb);
         const int nc = nc_index(fb);
         bool ok;
         if (ka == 0 && kb == 0) ok = put(VV + bfn * NREG + lv, la | (lb << 16));
@@ -168,12 +174,12 @@ __device__ int compile_fx(NodeSmem& ns, bool single_out, uint2* prog, int cap) {
       const int nc = nc_index(fb);
       if (kb <= 1) {  // b is a leaf, a is in G[lv]
         x = (modi ? (kb == 0 ? BV_M : BC_M) : (kb == 0 ? BV : BC)) + bfn * NREG + lv;
-        y = ns.leaf[cb];
+        y = ns.leaf(cb);
       } else if (ka <= 1) {  // a is a leaf, b is in G[lv]
         if (modi) x = (ka == 0 ? RV_M : RC_M) + bfn * NREG + lv;
         else if (nc < 0) x = (ka == 0 ? BV : BC) + bfn * NREG + lv;
         else x = (ka == 0 ? RV : RC) + nc * NREG + lv;
-        y = ns.leaf[ca];
+        y = ns.leaf(ca);
       } else {
         const bool a_first = ns.need[ca] >= ns.need[cb];
         const int first = a_first ? ca : cb, second = a_first ? cb : ca;
@@ -255,7 +261,7 @@ __device__ int compile_adj(NodeSmem& ns, bool single_out, uint2* prog) {
           ins.x = var ? OP_LDV : OP_LDC;
           last_ldv = var ? pc : -1;
         }
-        ins.y = ns.leaf[n];
+        ins.y = ns.leaf(n);
         ins.x |= (uint32_t)n << 16;  // leaf node index (constant gradients)
         prog[pc++] = ins;
         down = false;
@@ -307,14 +313,14 @@ __device__ int compile_adj(NodeSmem& ns, bool single_out, uint2* prog) {
       bool var = kind_of(ns.info[cb]) == 0;
       ins.x = (modi ? (var ? OP_BV_M : OP_BC_M) : (var ? OP_BV : OP_BC)) + f;
       ins.x |= modi ? o8 : 0;
-      ins.y = ns.leaf[cb];
+      ins.y = ns.leaf(cb);
       ins.x |= (uint32_t)cb << 16;
     } else if (la) {
       bool var = kind_of(ns.info[ca]) == 0;
       if (modi) ins.x = ((var ? OP_RV_M : OP_RC_M) + f) | o8;
       else if (f == F_ADD || f == F_MUL) ins.x = (var ? OP_BV : OP_BC) + f;
       else ins.x = (var ? OP_RV : OP_RC) + f;
-      ins.y = ns.leaf[ca];
+      ins.y = ns.leaf(ca);
       ins.x |= (uint32_t)ca << 16;
     } else {
       int d = ns.slot[q];
@@ -345,6 +351,7 @@ __global__ void __launch_bounds__(STAGE_WARPS * 32) stage_kernel(const __grid_co
     const float* T = a.type + p * a.ld;
     const float* V = a.val + p * a.ld;
     const float* S = a.size + p * a.ld;
+    ns.V = V;
     int len = 0;
     if (lane == 0) {
       float s0 = S[0];
@@ -360,7 +367,7 @@ __global__ void __launch_bounds__(STAGE_WARPS * 32) stage_kernel(const __grid_co
       for (int i = lane; i < len; i += 32) {
         float tv = T[i], vv = V[i], sv = S[i];
         int ty = is_int(tv) && tv >= 0.0f && tv < 64.0f ? (int)tv : -1;
-        uint32_t info = 0, leaf = 0;
+        uint32_t info = 0;
         int base = ty >= 0 ? (ty & ~T_MODI) : -1;
         bool modi = ty >= 0 && (ty & T_MODI);
         if (!(ty == 0 || ty == 1 || ty == 2 || ty == 3 || ty == 4 || ty == 18 || ty == 19 ||
@@ -368,11 +375,9 @@ __global__ void __launch_bounds__(STAGE_WARPS * 32) stage_kernel(const __grid_co
           st |= S_TYPE;
         } else if (base == T_VAR) {
           if (!is_int(vv) || vv < 0.0f || vv >= (float)a.n_features) st |= S_VAR;
-          else leaf = (uint32_t)vv;
           info = 0u << 4;
         } else if (base == T_CONST) {
           if (!isfinite(vv)) st |= S_CONST;
-          leaf = __float_as_uint(vv);
           info = 1u << 4;
         } else {
           if (!is_int(vv) || vv < 0.0f || vv >= 65536.0f) {
@@ -393,7 +398,6 @@ __global__ void __launch_bounds__(STAGE_WARPS * 32) stage_kernel(const __grid_co
           }
         }
         ns.info[i] = info;
-        ns.leaf[i] = leaf;
         ns.sz[i] = (is_int(sv) && sv >= 1.0f && sv <= (float)(len - i)) ? (int16_t)sv : (int16_t)0;
       }
       st = __reduce_or_sync(0xffffffffu, st);
@@ -441,34 +445,54 @@ __global__ void __launch_bounds__(STAGE_WARPS * 32) stage_kernel(const __grid_co
     }
 
     int pc = 0;
-    if (st == 0 && lane == 0) {
-      // ---- registers needed per subtree (bottom-up)
-      for (int i = len - 1; i >= 0; --i) {
-        int k = kind_of(ns.info[i]);
-        int nd;
-        if (k <= 1) {
-          nd = 1;
-        } else if (k == 2) {
-          nd = ns.need[i + 1];
-        } else {
-          // a binary node's operands, or an ite node's branches (its
-          // condition is evaluated first at the same level, then popped)
-          int ca, cb;
-          bin_ops(ns, i, &ca, &cb);
-          bool la = kind_of(ns.info[ca]) <= 1, lb = kind_of(ns.info[cb]) <= 1;
-          if (lb) nd = ns.need[ca];
-          else if (la) nd = ns.need[cb];
-          else {
-            int na = ns.need[ca], nb = ns.need[cb];
-            nd = na >= nb ? max(na, nb + 1) : max(nb, na + 1);
-          }
-          if (k == 4) nd = max(nd, (int)ns.need[i + 1]);
-        }
-        ns.need[i] = (uint8_t)min(nd, 255);
+    bool ternary = false;
+    if (st == 0) {
+      // ---- registers needed per subtree (bottom-up), lane-parallel over
+      // blocks of 32 nodes from the end: a node is done once its children
+      // (all at larger indices) are, so a block takes as many rounds as its
+      // longest parent chain
+      for (int i = lane; i < len; i += 32) {
+        ns.need[i] = 0;  // 0 = not known yet (every subtree needs >= 1)
+        ternary |= kind_of(ns.info[i]) == 4;
       }
+      ternary = __any_sync(0xffffffffu, ternary);
+      __syncwarp();
+      for (int base = (len - 1) & ~31; base >= 0; base -= 32) {
+        const int i = base + lane;
+        bool todo = i < len;
+        while (__any_sync(0xffffffffu, todo)) {
+          if (todo) {
+            const int k = kind_of(ns.info[i]);
+            int nd = 0;
+            if (k <= 1) {
+              nd = 1;
+            } else if (k == 2) {
+              nd = ns.need[i + 1];
+            } else {
+              // a binary node's operands, or an ite node's branches (its
+              // condition is evaluated first at the same level, then popped)
+              int ca, cb;
+              bin_ops(ns, i, &ca, &cb);
+              const int na = ns.need[ca], nb = ns.need[cb], nc = k == 4 ? ns.need[i + 1] : 1;
+              if (na && nb && nc) {
+                const bool la = kind_of(ns.info[ca]) <= 1, lb = kind_of(ns.info[cb]) <= 1;
+                if (lb) nd = na;
+                else if (la) nd = nb;
+                else nd = na >= nb ? max(na, nb + 1) : max(nb, na + 1);
+                if (k == 4) nd = max(nd, nc);
+              }
+            }
+            if (nd) {
+              ns.need[i] = (uint8_t)min(nd, 255);
+              todo = false;
+            }
+          }
+          __syncwarp();
+        }
+      }
+    }
+    if (st == 0 && lane == 0) {
       uint2* prog = a.prog + p * a.pcap;
-      bool ternary = false;
-      for (int i = 0; i < len; ++i) ternary |= kind_of(ns.info[i]) == 4;
       if (!a.want_nodes) {
         pc = compile_fx(ns, a.n_outputs == 1 && !modi_here, prog, a.pcap);
       } else if (ternary) {
