@@ -509,7 +509,7 @@ def part_modi(dev, a, index, peaks):
                     "forward + MSE (all points); forward + adjoint on every 10th point",
         "node_points": units, "steps": steps,
         "ms_forward_mse": ms_f, "node_points_per_s_forward": units / (ms_f / 1e3),
-        "roofline": _roofline(units, t_fp32, t_sfu, t_mem, ms_f, "eval_kernel<4,24,modi,mse> (whole call)",
+        "roofline": _roofline(units, t_fp32, t_sfu, t_mem, ms_f, "eval_kernel<4,28,modi,mse> (whole call)",
                               sms, sm_max_mhz, hbm_gbs, peak_kind),
         "fwd_bwd_points": int(Xs.shape[0]), "ms_fwd_bwd_sample": ms_fb,
         "ms_fwd_bwd_extrapolated_all_points": ms_fb * D / Xs.shape[0],
