@@ -39,6 +39,11 @@ The FP32 function bodies:
   plog(a)       |a| > 1e-6f ? lg2.approx(|a|) * ln2 : 0
   cexp(a)       ex2.approx.ftz(min(a, 80) * log2 e)
   tan(a)        sin.approx(r) * rcp.approx(cos.approx(r))
+Every add, sub, mul and fma of these bodies (and of the Modi accumulation)
+runs on two points at once as the packed f32x2 form, each half rounded like
+the scalar instruction; the issue slots it saves are what bounds this
+interpreter.  max, the guards and the approximations stay scalar (PTX has no
+packed form of them).
 
 The OP_* constants below are the accumulator-and-slots instruction set that
 the adjoint kernel runs (tgp_internal.cuh, enum Op); gen_interp_bwd.py
@@ -243,15 +248,14 @@ class Gen:
                 self.e(f"selp.f32 {out(j)}, {a(j)}, {b(j)}, P{j};")
             self.e(f"shr.b64 r_cs, r_cs, {self.K};")
             return
+        if f in (F_ADD, F_SUB, F_MUL):
+            name = {F_ADD: "add", F_SUB: "sub", F_MUL: "mul"}[f]
+            for h in range(self.K // 2):
+                self.p2(f"{name}.rn.f32x2", out, h, a, b)
+            return
         for j in range(self.K):
             o, x, y = out(j), a(j), b(j)
-            if f == F_ADD:
-                self.e(f"add.rn.f32 {o}, {x}, {y};")
-            elif f == F_SUB:
-                self.e(f"sub.rn.f32 {o}, {x}, {y};")
-            elif f == F_MUL:
-                self.e(f"mul.rn.f32 {o}, {x}, {y};")
-            elif f == F_MAX:
+            if f == F_MAX:
                 self.e(f"max.f32 {o}, {x}, {y};")
             elif f == F_PDIV:
                 # a * rcp(b) in flush-to-zero arithmetic: for |b| > 2^126
@@ -260,42 +264,75 @@ class Gen:
                 self.e(f"abs.f32 V{j}, {y};")
                 self.e(f"setp.gt.f32 P{j}, V{j}, {GUARD};")
                 self.e(f"rcp.approx.ftz.f32 V{j}, {y};")
-                self.e(f"mul.rn.f32 V{j}, {x}, V{j};")
-                self.e(f"selp.f32 {o}, V{j}, {ONE}, P{j};")
+        if f == F_PDIV:
+            V = self.named("V")
+            for h in range(self.K // 2):
+                self.p2("mul.rn.f32x2", V, h, a, V)
+            for j in range(self.K):
+                self.e(f"selp.f32 {out(j)}, V{j}, {ONE}, P{j};")
 
-    def reduce(self, j, x):
-        """V{j} = x reduced by 2pi (Cody-Waite), using W{j} as scratch."""
-        self.e(f"mul.rn.f32 W{j}, {x}, {INV2PI};")
-        self.e(f"add.rn.f32 W{j}, W{j}, {MAGIC};")
-        self.e(f"sub.rn.f32 W{j}, {MAGIC}, W{j};")       # -rint(x / 2pi)
-        self.e(f"fma.rn.f32 V{j}, W{j}, {C1}, {x};")
-        self.e(f"fma.rn.f32 V{j}, W{j}, {C2}, V{j};")
+    # ---- packed FP32 (f32x2: two points per instruction, each rounded as
+    # the scalar operation would be)
+    def pair(self, src, h):
+        """A .b64 operand holding src's points 2h and 2h+1: a packed register
+        pair, or a constant (hex float literal) in both halves."""
+        if isinstance(src, str):
+            return "0x" + src[2:] * 2
+        return "{" + f"{src(2 * h)}, {src(2 * h + 1)}" + "}"
+
+    def p2(self, op, out, h, *srcs):
+        """out[2h, 2h+1] = op(srcs...) on the pair of points 2h, 2h+1."""
+        names = []
+        for i, s_ in enumerate(srcs):
+            self.e(f"mov.b64 QP{i}, {self.pair(s_, h)};")
+            names.append(f"QP{i}")
+        self.e(f"{op} QP3, {', '.join(names)};")
+        self.e(f"mov.b64 {{{out(2 * h)}, {out(2 * h + 1)}}}, QP3;")
+
+    def reduce(self, a):
+        """V[j] = a[j] reduced by 2pi (Cody-Waite), W[j] scratch, two points
+        per instruction."""
+        V, W = self.named("V"), self.named("W")
+        for h in range(self.K // 2):
+            self.p2("mul.rn.f32x2", W, h, a, INV2PI)
+            self.p2("add.rn.f32x2", W, h, W, MAGIC)
+            self.p2("sub.rn.f32x2", W, h, MAGIC, W)      # -rint(x / 2pi)
+            self.p2("fma.rn.f32x2", V, h, W, C1, a)
+            self.p2("fma.rn.f32x2", V, h, W, C2, V)
 
     def fn1(self, f, out, a):
-        for j in range(self.K):
-            o, x = out(j), a(j)
-            if f == F_SIN:
-                self.reduce(j, x)
-                self.e(f"sin.approx.ftz.f32 {o}, V{j};")
-            elif f == F_COS:
-                self.reduce(j, x)
-                self.e(f"cos.approx.ftz.f32 {o}, V{j};")
-            elif f == F_PLOG:
-                self.e(f"abs.f32 V{j}, {x};")
+        K = self.K
+        V, W = self.named("V"), self.named("W")
+        if f in (F_SIN, F_COS, F_TAN):
+            self.reduce(a)
+            for j in range(K):
+                if f == F_SIN:
+                    self.e(f"sin.approx.ftz.f32 {out(j)}, V{j};")
+                elif f == F_COS:
+                    self.e(f"cos.approx.ftz.f32 {out(j)}, V{j};")
+                else:
+                    self.e(f"cos.approx.ftz.f32 W{j}, V{j};")
+                    self.e(f"sin.approx.ftz.f32 V{j}, V{j};")
+                    self.e(f"rcp.approx.ftz.f32 W{j}, W{j};")
+            if f == F_TAN:
+                for h in range(K // 2):
+                    self.p2("mul.rn.f32x2", out, h, V, W)
+        elif f == F_PLOG:
+            for j in range(K):
+                self.e(f"abs.f32 V{j}, {a(j)};")
                 self.e(f"setp.gt.f32 P{j}, V{j}, {GUARD};")
                 self.e(f"lg2.approx.ftz.f32 V{j}, V{j};")
-                self.e(f"mul.rn.f32 V{j}, V{j}, {LN2};")
-                self.e(f"selp.f32 {o}, V{j}, {ZERO}, P{j};")
-            elif f == F_CEXP:
-                self.e(f"min.f32 V{j}, {x}, {CLAMP};")
-                self.e(f"mul.rn.f32 V{j}, V{j}, {LOG2E};")
-                self.e(f"ex2.approx.ftz.f32 {o}, V{j};")
-            elif f == F_TAN:
-                self.reduce(j, x)
-                self.e(f"cos.approx.ftz.f32 W{j}, V{j};")
-                self.e(f"sin.approx.ftz.f32 V{j}, V{j};")
-                self.e(f"rcp.approx.ftz.f32 W{j}, W{j};")
-                self.e(f"mul.rn.f32 {o}, V{j}, W{j};")
+            for h in range(K // 2):
+                self.p2("mul.rn.f32x2", V, h, V, LN2)
+            for j in range(K):
+                self.e(f"selp.f32 {out(j)}, V{j}, {ZERO}, P{j};")
+        elif f == F_CEXP:
+            for j in range(K):
+                self.e(f"min.f32 V{j}, {a(j)}, {CLAMP};")
+            for h in range(K // 2):
+                self.p2("mul.rn.f32x2", V, h, V, LOG2E)
+            for j in range(K):
+                self.e(f"ex2.approx.ftz.f32 {out(j)}, V{j};")
 
     def modi_add(self, src):
         """out[o][lane points] += src[j] (o from bits 16..23 of the word)."""
@@ -306,8 +343,12 @@ class Gen:
             regs = [f"M{4 * h + q}" for q in range(4)]
             off = f"+{512 * h}" if h else ""
             self.e(f"ld.shared.v4.f32 {{{', '.join(regs)}}}, [r_ma{off}];")
-            for q in range(4):
-                self.e(f"add.rn.f32 {regs[q]}, {regs[q]}, {src(4 * h + q)};")
+        M = self.named("M")
+        for h in range(K // 2):
+            self.p2("add.rn.f32x2", M, h, M, src)
+        for h in range(K // 4):
+            regs = [f"M{4 * h + q}" for q in range(4)]
+            off = f"+{512 * h}" if h else ""
             self.e(f"st.shared.v4.f32 [r_ma{off}], {{{', '.join(regs)}}};")
 
     def cond(self, src, scalar=False):
@@ -364,6 +405,7 @@ class Gen:
         self.e(".reg .f32 " + ", ".join(temps) + ", cv, c2v;")
         self.e(".reg .f32 " + ", ".join(G(d)(j) for d in range(NREG) for j in range(K)) + ";")
         self.e(".reg .pred " + ", ".join(f"P{j}" for j in range(K)) + ";")
+        self.e(".reg .b64 QP0, QP1, QP2, QP3;")
         self.e(".reg .u32 r_ptr, r_ix, r_iy, r_nx, r_ny, r_op, r_ad, r_xc, r_xstr, r_mo, r_moo, "
                "r_ma, r_flag, r_t, r_sp, r_sb, r_c, r_cb, r_ct;")
         self.e(".reg .b64 r_cs, r_cb64;")

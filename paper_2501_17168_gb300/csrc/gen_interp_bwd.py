@@ -30,6 +30,9 @@ derivatives on their constant branches):
 Modi nodes (Sec. IV-C): the function value's adjoint is the seed of its
 output; the value handed to the parent (the rightmost child) keeps the
 parent's adjoint.
+As in the forward interpreter, the adds, subtractions, multiplies and fmas
+run as packed f32x2 pairs of points; the per-warp sums of constant
+gradients keep their scalar order.
 """
 from __future__ import annotations
 
@@ -78,23 +81,44 @@ class Base:
             regs = ", ".join(dst(4 * h + q) for q in range(4))
             self.e(f"ld.local.v4.f32 {{{regs}}}, [r_tape+{16 * h}];")
 
-    def reduce(self, j, x):
-        self.e(f"mul.rn.f32 W{j}, {x}, {INV2PI};")
-        self.e(f"add.rn.f32 W{j}, W{j}, {MAGIC};")
-        self.e(f"sub.rn.f32 W{j}, {MAGIC}, W{j};")
-        self.e(f"fma.rn.f32 V{j}, W{j}, {C1}, {x};")
-        self.e(f"fma.rn.f32 V{j}, W{j}, {C2}, V{j};")
+    # ---- packed FP32 (f32x2: two points per instruction, each rounded as
+    # the scalar operation would be)
+    @staticmethod
+    def pair(src, h):
+        if isinstance(src, str):          # a constant (hex float literal) in both halves
+            return "0x" + src[2:] * 2
+        return "{" + f"{src(2 * h)}, {src(2 * h + 1)}" + "}"
+
+    def p2(self, op, out, h, *srcs):
+        """out[2h, 2h+1] = op(srcs...) on the pair of points 2h, 2h+1."""
+        names = []
+        for i, s_ in enumerate(srcs):
+            self.e(f"mov.b64 QP{i}, {self.pair(s_, h)};")
+            names.append(f"QP{i}")
+        self.e(f"{op} QP3, {', '.join(names)};")
+        self.e(f"mov.b64 {{{out(2 * h)}, {out(2 * h + 1)}}}, QP3;")
+
+    def pk(self, op, out, *srcs):
+        for h in range(self.K // 2):
+            self.p2(op, out, h, *srcs)
+
+    def reduce(self, a):
+        """V[j] = a[j] reduced by 2pi (Cody-Waite), W[j] scratch."""
+        V, W = self.vec("V"), self.vec("W")
+        for h in range(self.K // 2):
+            self.p2("mul.rn.f32x2", W, h, a, INV2PI)
+            self.p2("add.rn.f32x2", W, h, W, MAGIC)
+            self.p2("sub.rn.f32x2", W, h, MAGIC, W)
+            self.p2("fma.rn.f32x2", V, h, W, C1, a)
+            self.p2("fma.rn.f32x2", V, h, W, C2, V)
 
     def fn2(self, f, out, a, b):
+        if f in (F_ADD, F_SUB, F_MUL):
+            self.pk({F_ADD: "add", F_SUB: "sub", F_MUL: "mul"}[f] + ".rn.f32x2", out, a, b)
+            return
         for j in range(self.K):
             o, x, y = out(j), a(j), b(j)
-            if f == F_ADD:
-                self.e(f"add.rn.f32 {o}, {x}, {y};")
-            elif f == F_SUB:
-                self.e(f"sub.rn.f32 {o}, {x}, {y};")
-            elif f == F_MUL:
-                self.e(f"mul.rn.f32 {o}, {x}, {y};")
-            elif f == F_MAX:
+            if f == F_MAX:
                 self.e(f"max.f32 {o}, {x}, {y};")
             elif f == F_PDIV:
                 # a * rcp(b) in flush-to-zero arithmetic: for |b| > 2^126
@@ -103,15 +127,20 @@ class Base:
                 self.e(f"abs.f32 V{j}, {y};")
                 self.e(f"setp.gt.f32 P{j}, V{j}, {GUARD};")
                 self.e(f"rcp.approx.ftz.f32 V{j}, {y};")
-                self.e(f"mul.rn.f32 V{j}, {x}, V{j};")
-                self.e(f"selp.f32 {o}, V{j}, {ONE}, P{j};")
+        if f == F_PDIV:
+            V = self.vec("V")
+            self.pk("mul.rn.f32x2", V, a, V)
+            for j in range(self.K):
+                self.e(f"selp.f32 {out(j)}, V{j}, {ONE}, P{j};")
 
     def fn1d(self, f, out, a, d):
-        """out[j] = f(a[j]) and d[j] = f'(a[j]) (d computed before out is written)."""
-        for j in range(self.K):
-            o, x, dd = out(j), a(j), d(j)
-            if f in (F_SIN, F_COS, F_TAN):
-                self.reduce(j, x)
+        """out[j] = f(a[j]) and d[j] = f'(a[j]) (a is read before out is written)."""
+        K = self.K
+        V, W = self.vec("V"), self.vec("W")
+        if f in (F_SIN, F_COS, F_TAN):
+            self.reduce(a)
+            for j in range(K):
+                o, dd = out(j), d(j)
                 if f == F_SIN:
                     self.e(f"cos.approx.ftz.f32 {dd}, V{j};")
                     self.e(f"sin.approx.ftz.f32 {o}, V{j};")
@@ -123,32 +152,42 @@ class Base:
                     self.e(f"cos.approx.ftz.f32 W{j}, V{j};")
                     self.e(f"sin.approx.ftz.f32 V{j}, V{j};")
                     self.e(f"rcp.approx.ftz.f32 W{j}, W{j};")
-                    self.e(f"mul.rn.f32 {o}, V{j}, W{j};")
-                    self.e(f"fma.rn.f32 {dd}, {o}, {o}, {ONE};")
-            elif f == F_PLOG:
+            if f == F_TAN:
+                self.pk("mul.rn.f32x2", out, V, W)
+                self.pk("fma.rn.f32x2", d, out, out, ONE)
+        elif f == F_PLOG:
+            for j in range(K):
+                x = a(j)
                 self.e(f"abs.f32 V{j}, {x};")
                 self.e(f"setp.gt.f32 P{j}, V{j}, {GUARD};")
                 self.e(f"rcp.approx.ftz.f32 W{j}, {x};")
-                self.e(f"selp.f32 {dd}, W{j}, {ZERO}, P{j};")
+                self.e(f"selp.f32 {d(j)}, W{j}, {ZERO}, P{j};")
                 self.e(f"lg2.approx.ftz.f32 V{j}, V{j};")
-                self.e(f"mul.rn.f32 V{j}, V{j}, {LN2};")
-                self.e(f"selp.f32 {o}, V{j}, {ZERO}, P{j};")
-            elif f == F_CEXP:
+            self.pk("mul.rn.f32x2", V, V, LN2)
+            for j in range(K):
+                self.e(f"selp.f32 {out(j)}, V{j}, {ZERO}, P{j};")
+        elif f == F_CEXP:
+            for j in range(K):
+                x = a(j)
                 self.e(f"setp.le.f32 P{j}, {x}, {CLAMP};")
                 self.e(f"min.f32 V{j}, {x}, {CLAMP};")
-                self.e(f"mul.rn.f32 V{j}, V{j}, {LOG2E};")
-                self.e(f"ex2.approx.ftz.f32 {o}, V{j};")
-                self.e(f"selp.f32 {dd}, {o}, {ZERO}, P{j};")
+            self.pk("mul.rn.f32x2", V, V, LOG2E)
+            for j in range(K):
+                self.e(f"ex2.approx.ftz.f32 {out(j)}, V{j};")
+                self.e(f"selp.f32 {d(j)}, {out(j)}, {ZERO}, P{j};")
 
     def modi_add(self, src):
         self.e("bfe.u32 r_moo, r_ix, 8, 8;")
         self.e(f"mad.lo.u32 r_ma, r_moo, {128 * self.K}, r_mo;")
+        M = self.vec("M")
         for h in range(self.K // 4):
             regs = [f"M{4 * h + q}" for q in range(4)]
             off = f"+{512 * h}" if h else ""
             self.e(f"ld.shared.v4.f32 {{{', '.join(regs)}}}, [r_ma{off}];")
-            for q in range(4):
-                self.e(f"add.rn.f32 {regs[q]}, {regs[q]}, {src(4 * h + q)};")
+        self.pk("add.rn.f32x2", M, M, src)
+        for h in range(self.K // 4):
+            regs = [f"M{4 * h + q}" for q in range(4)]
+            off = f"+{512 * h}" if h else ""
             self.e(f"st.shared.v4.f32 [r_ma{off}], {{{', '.join(regs)}}};")
 
 
@@ -168,6 +207,7 @@ class Fwd(Base):
         self.e("{")
         self.e(".reg .f32 " + ", ".join(regs) + ", cv;")
         self.e(".reg .pred " + ", ".join(f"P{j}" for j in range(K)) + ";")
+        self.e(".reg .b64 QP0, QP1, QP2, QP3;")
         self.e(".reg .u32 r_ptr, r_ix, r_iy, r_nx, r_ny, r_op, r_ad, r_xc, r_xstr, r_mo, r_moo, r_ma, r_flag, r_tape, r_slot, r_d, r_sl;")
         self.e("mov.u32 r_slot, %{slot};")
         self.e("mov.u32 r_ptr, %{pg};")
@@ -380,7 +420,30 @@ class Rev(Base):
 
     def dfn2(self, f, a, b, g, da, db):
         """da[j] = g*df/da, db[j] = g*df/db at (a[j], b[j]); None skips one"""
-        for j in range(self.K):
+        K = self.K
+        if f == F_MUL:
+            if da: self.pk("mul.rn.f32x2", da, g, b)
+            if db: self.pk("mul.rn.f32x2", db, g, a)
+            return
+        if f == F_PDIV:
+            V, W = self.vec("V"), self.vec("W")
+            for j in range(K):
+                y = b(j)
+                self.e(f"abs.f32 V{j}, {y};")
+                self.e(f"setp.gt.f32 P{j}, V{j}, {GUARD};")
+                self.e(f"rcp.approx.ftz.f32 V{j}, {y};")
+            self.pk("mul.rn.f32x2", W, g, V)                  # g / b
+            if db:
+                self.pk("mul.rn.f32x2", V, a, V)              # a / b
+                self.pk("mul.rn.f32x2", V, W, V)
+                for j in range(K):
+                    self.e(f"neg.f32 V{j}, V{j};")
+                    self.e(f"selp.f32 {db(j)}, V{j}, {ZERO}, P{j};")
+            if da:
+                for j in range(K):
+                    self.e(f"selp.f32 {da(j)}, W{j}, {ZERO}, P{j};")
+            return
+        for j in range(K):
             x, y, gg = a(j), b(j), g(j)
             if f == F_ADD:
                 if da: self.e(f"mov.f32 {da(j)}, {gg};")
@@ -388,21 +451,6 @@ class Rev(Base):
             elif f == F_SUB:
                 if da: self.e(f"mov.f32 {da(j)}, {gg};")
                 if db: self.e(f"neg.f32 {db(j)}, {gg};")
-            elif f == F_MUL:
-                if da: self.e(f"mul.rn.f32 {da(j)}, {gg}, {y};")
-                if db: self.e(f"mul.rn.f32 {db(j)}, {gg}, {x};")
-            elif f == F_PDIV:
-                self.e(f"abs.f32 V{j}, {y};")
-                self.e(f"setp.gt.f32 P{j}, V{j}, {GUARD};")
-                self.e(f"rcp.approx.ftz.f32 V{j}, {y};")
-                self.e(f"mul.rn.f32 W{j}, {gg}, V{j};")          # g / b
-                if db:
-                    self.e(f"mul.rn.f32 V{j}, {x}, V{j};")       # a / b
-                    self.e(f"mul.rn.f32 V{j}, W{j}, V{j};")
-                    self.e(f"neg.f32 V{j}, V{j};")
-                    self.e(f"selp.f32 {db(j)}, V{j}, {ZERO}, P{j};")
-                if da:
-                    self.e(f"selp.f32 {da(j)}, W{j}, {ZERO}, P{j};")
             elif f == F_MAX:
                 self.e(f"setp.ge.f32 P{j}, {x}, {y};")
                 self.e(f"setp.nan.f32 Q{j}, {y}, {y};")
@@ -411,8 +459,7 @@ class Rev(Base):
                 if db: self.e(f"selp.f32 {db(j)}, {ZERO}, {gg}, P{j};")
 
     def addv(self, out, x, y):
-        for j in range(self.K):
-            self.e(f"add.f32 {out(j)}, {x(j)}, {y(j)};")
+        self.pk("add.rn.f32x2", out, x, y)
 
     def build(self):
         K = self.K
@@ -424,6 +471,7 @@ class Rev(Base):
         self.e("{")
         self.e(".reg .f32 " + ", ".join(regs) + ", cv, q_s, q_t;")
         self.e(".reg .pred " + ", ".join([f"P{j}" for j in range(K)] + [f"Q{j}" for j in range(K)]) + ", PL;")
+        self.e(".reg .b64 QP0, QP1, QP2, QP3;")
         self.e(".reg .u32 r_ptr, r_ix, r_iy, r_nx, r_ny, r_op, r_ad, r_xc, r_xstr, r_gx, r_cg, r_sd, r_moo, r_ma, r_tape, r_nd, r_ca, r_lane, r_beg, r_slot, r_d, r_sl;")
         self.e("mov.u32 r_slot, %{slot};")
         self.e("mov.u32 r_ptr, %{plast};")
@@ -476,13 +524,11 @@ class Rev(Base):
         for f in UNA:
             def un(f=f):
                 self.tape_get(T1)
-                for j in range(K):
-                    self.e(f"mul.rn.f32 G{j}, G{j}, T{j};")
+                self.pk("mul.rn.f32x2", G, G, T1)
 
             def unv(f=f):
                 self.tape_get(T1)
-                for j in range(K):
-                    self.e(f"mul.rn.f32 DA{j}, G{j}, T{j};")
+                self.pk("mul.rn.f32x2", DA, G, T1)
                 self.gx_add(DA)
 
             def unm(f=f):
@@ -490,8 +536,7 @@ class Rev(Base):
                     return
                 self.tape_get(T1)
                 self.seed(SD)
-                for j in range(K):
-                    self.e(f"fma.rn.f32 G{j}, SD{j}, T{j}, G{j};")
+                self.pk("fma.rn.f32x2", G, SD, T1, G)
 
             self.case(OP_UN + f - F_SIN, un)
             self.e(f"RC{OP_UNV + f - F_SIN}:")
