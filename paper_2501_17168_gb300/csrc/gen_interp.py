@@ -126,7 +126,17 @@ MEM_FORMS = [
     ("SAVES", NSM),                               # the same for entry s < NSM in shared memory
     ("MSS", NB * NSM), ("SMS", 3 * NSM),          #   (sub = f * NSM + s)
     ("MSS_M", NB * NSM), ("SMS_M", NB * NSM),
+    ("PUSHS", None), ("PUSHL", None),             # push G[NREG-1] (shared-memory entry 0 / local
+                                                  # memory), then run a subtree's first instruction
 ]
+# The forms that can start a subtree (its first instruction loads a leaf), in
+# the order of the PUSHS/PUSHL sub-forms: the instruction after a push is
+# always one of these at level NREG-1, so the push rides in its word
+START_FORMS = [("LDV", 1), ("LDC", 1), ("CDV", 1), ("CDC", 1), ("UNV", 5), ("UNC", 5),
+               ("UNV_M", 5), ("UNC_M", 5), ("VV", NB), ("VC", NB), ("CV", 3), ("CC", NB)]
+NSTART = sum(n for _, n in START_FORMS)
+assert NSM == 1  # the fused pushes address shared-memory entry 0 only
+MEM_FORMS = [(name, NSTART if n is None else n) for name, n in MEM_FORMS]
 MAXC = 8          # pending ite conditions: 64 condition bits, 8 points per lane
 
 
@@ -612,6 +622,17 @@ class Gen:
                     self.case(fx("MSS_M", bi(f) * NSM + q, 0), lambda q=q: sm_pop(q), then=f"MSMB{f}")
                     self.case(fx("SMS_M", bi(f) * NSM + q, 0), lambda q=q: sm_pop(q), then=f"SMMB{f}")
 
+        # a push fused into the first instruction of the subtree that follows
+        # it: store G[NREG-1], then go on in that instruction's own case
+        i = 0
+        for name, n in START_FORMS:
+            for sub in range(n):
+                target = fx(name, sub, top)
+                if target in self.defined:
+                    self.case(fx("PUSHS", i, 0), lambda: sm_push(0), then=target)
+                    self.case(fx("PUSHL", i, 0), lambda: self.mem_push(Gt), then=target)
+                i += 1
+
         # the cases in code order (see layout_key)
         for _, chunk in sorted(self.chunks, key=lambda c: c[0]):
             self.lines.extend(chunk)
@@ -696,6 +717,19 @@ def render_isa() -> str:
     out.append("// index of a binary form's function (ite's branch selection after the binary functions)")
     out.append("__host__ __device__ constexpr int bin_index(int f) { return f <= 4 ? f : f == 10 ? 5 : -1; }")
     out.append(f"constexpr int MAXC = {MAXC};   // pending ite conditions the 64-bit condition stack holds")
+    out.append(f"constexpr int NSTART = {NSTART};  // forms that can start a subtree (PUSHS/PUSHL sub-forms)")
+    out.append("// The fused form \"push G[NREG-1] (to shared-memory entry 0, or to local")
+    out.append("// memory when `local`), then run op\" for a subtree's first instruction op at")
+    out.append("// level NREG-1; 0 when op has none (the push is then a word of its own).")
+    out.append("__host__ __device__ constexpr uint32_t push_form(uint32_t op, bool local) {")
+    out.append("  const uint32_t pb = local ? PUSHL : PUSHS;")
+    i = 0
+    for name, n in START_FORMS:
+        out.append(f"  if (op >= {name} && op < {name} + {n} * NREG && (op - {name}) % NREG == NREG - 1)")
+        out.append(f"    return pb + {i} + (op - {name}) / NREG;")
+        i += n
+    out.append("  return 0;")
+    out.append("}")
     out.append("}  // namespace fx")
     out.append("}  // namespace tgp")
     return "\n".join(out) + "\n"

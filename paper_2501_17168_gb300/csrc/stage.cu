@@ -58,8 +58,9 @@ __device__ __forceinline__ int kind_of(uint32_t in) { return (in >> 4) & 7; }
 // goes to register group G[d]; of a binary node's two subtrees the one that
 // needs more levels is evaluated first at the node's level, the other one
 // level deeper (at level NREG-1 the first result is saved to the memory
-// stack instead and the other subtree reuses the level).  Leaf operands ride
-// in their parent's instruction.  Returns the number of words, or -1 if the
+// stack instead and the other subtree reuses the level; the push rides in
+// the word of that subtree's first instruction).  Leaf operands ride in
+// their parent's instruction.  Returns the number of words, or -1 if the
 // program would exceed cap words or the memory stack (neither happens for
 // trees of up to 1024 nodes: every non-leaf subtree has a leaf without a
 // word of its own, and the Sethi-Ullman number stays below NREG + MAXS).
@@ -76,14 +77,29 @@ __device__ __forceinline__ void bin_ops(const NodeSmem& ns, int q, int* ca, int*
   *cb = a + ns.sz[a];
 }
 
+static_assert(fx::NSM == 1, "fused pushes address shared-memory entry 0 only");
+
 __device__ int compile_fx(NodeSmem& ns, bool single_out, uint2* prog, int cap) {
   using namespace fx;
   int pc = 0, n = 0, sdepth = 0, cdepth = 0;
+  int pend = 0;  // a push of G[NREG-1] not yet emitted: 1 to shared-memory entry 0, 2 to local memory
   bool down = true;
   auto put = [&](uint32_t x, uint32_t y) {
     if (pc >= cap) return false;
     prog[pc++] = make_uint2(x, y);
     return true;
+  };
+  // the first word of an instruction: a pending push rides in it (the
+  // instruction after a push starts the next subtree at level NREG-1, so it
+  // loads a leaf and has a fused push form); else the push is a word of its own
+  auto emit = [&](uint32_t x, uint32_t y) {
+    if (pend) {
+      const uint32_t fused = push_form(x & 0xFFFFu, pend == 2);
+      if (fused) x = fused | (x & ~0xFFFFu);
+      else if (!put(pend == 1 ? (uint32_t)SAVES : (uint32_t)SAVE, 0)) return false;
+      pend = 0;
+    }
+    return put(x, y);
   };
   ns.slot[0] = 0;
   for (;;) {
@@ -92,7 +108,7 @@ __device__ int compile_fx(NodeSmem& ns, bool single_out, uint2* prog, int cap) {
     if (down) {
       const int lv = ns.slot[n];
       if (k <= 1) {  // a lone leaf: the root, or the first operand of a Modi node
-        if (!put((k == 0 ? LDV : LDC) + lv, ns.leaf(n))) return -1;
+        if (!emit((k == 0 ? LDV : LDC) + lv, ns.leaf(n))) return -1;
         down = false;
         continue;
       }
@@ -103,7 +119,7 @@ __device__ int compile_fx(NodeSmem& ns, bool single_out, uint2* prog, int cap) {
         const int c = n + 1, ck = kind_of(ns.info[c]);
         if (ck <= 1) {  // unary of a leaf: one instruction
           const uint32_t base = modi ? (ck == 0 ? UNV_M : UNC_M) : (ck == 0 ? UNV : UNC);
-          if (!put((base + (f - F_SIN) * NREG + lv) | o16, ns.leaf(c))) return -1;
+          if (!emit((base + (f - F_SIN) * NREG + lv) | o16, ns.leaf(c))) return -1;
           down = false;
           continue;
         }
@@ -116,7 +132,7 @@ __device__ int compile_fx(NodeSmem& ns, bool single_out, uint2* prog, int cap) {
         // the condition stack and the branches follow as a binary form
         const int a = n + 1, ka = kind_of(ns.info[a]);
         if (ka <= 1) {
-          if (cdepth >= MAXC || !put((ka == 0 ? CDV : CDC) + lv, ns.leaf(a))) return -1;
+          if (cdepth >= MAXC || !emit((ka == 0 ? CDV : CDC) + lv, ns.leaf(a))) return -1;
           ++cdepth;
           ns.info[n] = in | COND_DONE;
           continue;
@@ -133,11 +149,11 @@ __device__ int compile_fx(NodeSmem& ns, bool single_out, uint2* prog, int cap) {
         const uint32_t la = ns.leaf(ca), lb = ns.leaf(cb);
         const int nc = nc_index(fb);
         bool ok;
-        if (ka == 0 && kb == 0) ok = put(VV + bfn * NREG + lv, la | (lb << 16));
-        else if (ka == 0) ok = put(VC + bfn * NREG + lv, lb) && put(la, 0);
-        else if (kb == 0 && nc < 0) ok = put(VC + bfn * NREG + lv, la) && put(lb, 0);
-        else if (kb == 0) ok = put(CV + nc * NREG + lv, la) && put(lb, 0);
-        else ok = put(CC + bfn * NREG + lv, la) && put(lb, 0);
+        if (ka == 0 && kb == 0) ok = emit(VV + bfn * NREG + lv, la | (lb << 16));
+        else if (ka == 0) ok = emit(VC + bfn * NREG + lv, lb) && put(la, 0);
+        else if (kb == 0 && nc < 0) ok = emit(VC + bfn * NREG + lv, la) && put(lb, 0);
+        else if (kb == 0) ok = emit(CV + nc * NREG + lv, la) && put(lb, 0);
+        else ok = emit(CC + bfn * NREG + lv, la) && put(lb, 0);
         if (!ok) return -1;
         if (k == 4) --cdepth;  // the selection pops the condition
         down = false;
@@ -156,7 +172,7 @@ __device__ int compile_fx(NodeSmem& ns, bool single_out, uint2* prog, int cap) {
     const bool modi = qin & 128;
     const uint32_t o16 = modi ? ((qin >> 8) & 255) << 16 : 0;
     if (qk == 4 && n == q + 1) {  // ite's condition is done: push its sign bits
-      if (cdepth >= MAXC || !put(CD + lv, 0)) return -1;
+      if (cdepth >= MAXC || !emit(CD + lv, 0)) return -1;
       ++cdepth;
       ns.info[q] = qin | COND_DONE;
       n = q;
@@ -186,7 +202,8 @@ __device__ int compile_fx(NodeSmem& ns, bool single_out, uint2* prog, int cap) {
         const bool mem = lv + 1 >= NREG;
         if (n == first) {  // first operand done: evaluate the second one
           if (mem) {
-            if (sdepth >= NSM + MAXS || !put(sdepth < NSM ? SAVES + sdepth : SAVE, 0)) return -1;
+            if (sdepth >= NSM + MAXS) return -1;
+            pend = sdepth < NSM ? 1 : 2;
             ++sdepth;
             ns.slot[second] = lv;
           } else {
@@ -221,10 +238,10 @@ __device__ int compile_fx(NodeSmem& ns, bool single_out, uint2* prog, int cap) {
       }
       if (qk == 4) --cdepth;  // the selection pops the condition
     }
-    if (!put(x | o16, y)) return -1;
+    if (!emit(x | o16, y)) return -1;
     n = q;
   }
-  if (!put(single_out ? END_ROOT : END_MODI, 0)) return -1;
+  if (!emit(single_out ? END_ROOT : END_MODI, 0)) return -1;
   return pc;
 }
 
