@@ -730,6 +730,26 @@ def render_isa() -> str:
         i += n
     out.append("  return 0;")
     out.append("}")
+    # the same map as a table for the stage compiler's serial emission loop
+    # (one constant-memory load instead of the range checks)
+    vals = []
+    for op in range(FX_COUNT):
+        v = 0
+        i = 0
+        for name, n in START_FORMS:
+            for sub in range(n):
+                if fx(name, sub, NREG - 1) == op:
+                    v = FX_BASE["PUSHS"] + i
+                i += 1
+        vals.append(v)
+    out.append("#ifdef __CUDACC__")
+    out.append("// push_form(op, false) for every opcode; push_form(op, true) is that + NSTART")
+    out.append("// where it is not 0")
+    out.append("static __constant__ uint16_t PUSH_FORM_TABLE[COUNT] = {")
+    for k in range(0, FX_COUNT, 16):
+        out.append("    " + ", ".join(str(v) for v in vals[k:k + 16]) + ",")
+    out.append("};")
+    out.append("#endif")
     out.append("}  // namespace fx")
     out.append("}  // namespace tgp")
     return "\n".join(out) + "\n"

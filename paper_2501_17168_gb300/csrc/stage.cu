@@ -94,8 +94,8 @@ __device__ int compile_fx(NodeSmem& ns, bool single_out, uint2* prog, int cap) {
   // loads a leaf and has a fused push form); else the push is a word of its own
   auto emit = [&](uint32_t x, uint32_t y) {
     if (pend) {
-      const uint32_t fused = push_form(x & 0xFFFFu, pend == 2);
-      if (fused) x = fused | (x & ~0xFFFFu);
+      uint32_t fused = PUSH_FORM_TABLE[x & 0xFFFFu];  // push_form(op, false)
+      if (fused) x = (fused + (pend == 2 ? (uint32_t)NSTART : 0u)) | (x & ~0xFFFFu);
       else if (!put(pend == 1 ? (uint32_t)SAVES : (uint32_t)SAVE, 0)) return false;
       pend = 0;
     }

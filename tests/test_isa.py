@@ -73,6 +73,20 @@ def test_header_push_form_matches_the_generator(header_push_form):
     assert n_fused == gi.NSTART
 
 
+def test_device_table_matches_push_form(header_push_form):
+    """The stage compiler reads the fused opcodes from a constant-memory
+    table; it must hold push_form(op, false) for every opcode."""
+    text = gi.render_isa()
+    body = text[text.index("PUSH_FORM_TABLE[COUNT] = {"):]
+    body = body[body.index("{") + 1:body.index("};")]
+    table = [int(t) for t in body.replace("\n", " ").split(",") if t.strip()]
+    assert len(table) == gi.FX_COUNT
+    for op, v in enumerate(table):
+        assert v == header_push_form[op][0], op
+        if v:
+            assert header_push_form[op][1] == v + gi.NSTART
+
+
 def test_fused_opcodes_are_distinct_and_in_range(header_push_form):
     seen = set()
     for s, l in header_push_form.values():
